@@ -1,0 +1,95 @@
+"""Seeded porosity fields (the coil represented as a porous medium).
+
+All fields are float32 arrays of shape (nz, ny, nx) with values in (0, 1].
+"""
+
+import numpy as np
+
+from . import geometry as geo
+
+
+def plug_porosity(flags, z0=24, z1=40, value=0.75):
+    """Porosity 1 everywhere except a plug of layers z0..z1 (inclusive)."""
+    phi = np.ones(flags.shape, dtype=np.float32)
+    phi[z0 : z1 + 1] = np.float32(value)
+    return phi
+
+
+def sac_random_porosity(n, small=False, seed=0, sigma=6.0, mean=0.75, amp=0.1,
+                        lo=0.6, hi=1.0):
+    """Coil porosity inside the sac: a Gaussian-smoothed random field.
+
+    i.i.d. N(0, 1) noise is drawn on the sac's bounding box padded by 4*sigma
+    (default_rng(seed)), filtered with a Gaussian of standard deviation
+    ``sigma`` voxels, rescaled to unit standard deviation, mapped to
+    ``mean + amp * z`` and clipped to [lo, hi].  It is applied inside the sac
+    sphere only; porosity is 1 elsewhere.
+    """
+    from scipy.ndimage import gaussian_filter
+
+    sc, r_s = geo.sac_sphere(n, small)
+    pad = int(np.ceil(r_s + 4 * sigma))
+    lo_c = [max(0, int(np.floor(c)) - pad) for c in sc]
+    hi_c = [min(n, int(np.ceil(c)) + pad + 1) for c in sc]
+    shape = (hi_c[2] - lo_c[2], hi_c[1] - lo_c[1], hi_c[0] - lo_c[0])
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal(shape)
+    field = gaussian_filter(noise, sigma=sigma, mode="reflect")
+    field /= field.std()
+    val = np.clip(mean + amp * field, lo, hi).astype(np.float32)
+    phi = np.ones((n, n, n), dtype=np.float32)
+    sub = phi[lo_c[2] : hi_c[2], lo_c[1] : hi_c[1], lo_c[0] : hi_c[0]]
+    sac = geo.sac_mask(n, small)[lo_c[2] : hi_c[2], lo_c[1] : hi_c[1], lo_c[0] : hi_c[0]] > 0
+    sub[sac] = val[sac]
+    return phi
+
+
+def wire_coil(n, packing=0.25, seed=0, thickness_radius=1, small=False):
+    """Seeded random-walk helical wire filling ``packing`` of the sac volume.
+
+    Unit steps; each direction is the previous one plus a helical bias (rotation
+    about the sac's radial axis) plus Gaussian jitter, reflected back when the
+    walker leaves the sac sphere.  The wire is deposited with a dilation radius
+    ``thickness_radius`` (a 2-voxel-thick wire for radius 1).  Returns a uint8
+    mask of wire voxels (inside the sac only).
+    """
+    sc, r_s = geo.sac_sphere(n, small)
+    sac = geo.sac_mask(n, small) > 0
+    target = int(packing * sac.sum())
+    wire = np.zeros_like(sac)
+    rng = np.random.default_rng(seed)
+    p = np.array(sc, dtype=np.float64)
+    d = rng.standard_normal(3)
+    d /= np.linalg.norm(d)
+    axis = np.array([0.0, 1.0, 0.0])
+    offs = [
+        (dz, dy, dx)
+        for dz in range(-thickness_radius, thickness_radius + 1)
+        for dy in range(-thickness_radius, thickness_radius + 1)
+        for dx in range(-thickness_radius, thickness_radius + 1)
+        if dx * dx + dy * dy + dz * dz <= thickness_radius * thickness_radius
+    ]
+    count = 0
+    max_steps = 200 * target + 1000
+    for _ in range(max_steps):
+        if count >= target:
+            break
+        helix = np.cross(axis, d)
+        d = d + 0.35 * helix + 0.25 * rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        q = p + d
+        if np.linalg.norm(q - sc) > r_s - thickness_radius - 0.5:
+            # reflect the direction about the sphere normal
+            nrm = (q - sc) / np.linalg.norm(q - sc)
+            d = d - 2.0 * np.dot(d, nrm) * nrm
+            q = p + d
+            if np.linalg.norm(q - sc) > r_s - thickness_radius - 0.5:
+                q = p
+        p = q
+        ix, iy, iz = (int(np.floor(c)) for c in p)
+        for dz, dy, dx in offs:
+            z, y, x = iz + dz, iy + dy, ix + dx
+            if 0 <= x < n and 0 <= y < n and 0 <= z < n and sac[z, y, x] and not wire[z, y, x]:
+                wire[z, y, x] = True
+                count += 1
+    return wire.astype(np.uint8)

@@ -1,0 +1,106 @@
+"""The two FP64 oracles (C push form, torch pull form) against each other, the
+Zou-He inlet against its defining momentum identity, and the torch reference
+gradient against central finite differences of the C oracle."""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from lbm_inputs import aneurysm_problem, periodic_box_problem, pipe_problem
+from lbm_inputs.configs import lattice_rheology
+from oracle.oracle import Oracle
+from oracle.torch_ref import TorchLBM
+
+
+def _compare(prob, steps):
+    o = Oracle(prob)
+    o.step(steps)
+    m = o.moments()
+    tl = TorchLBM(prob)
+    phi = torch.tensor(prob.phi.astype(np.float64))
+    f, om = tl.run(phi, steps)
+    fl = tl.fields(f, om, phi)
+    umax = max(np.abs(m["u"]).max(), 1e-30)
+    assert np.abs(fl["u"].numpy() - m["u"]).max() < 1e-12 * umax + 1e-15  # f ~ w: absolute round-off of sum f c
+    assert np.abs(fl["rho"].numpy() - m["rho"]).max() < 1e-13
+    gmax = max(m["gdot"].max(), 1e-30)
+    assert np.abs(fl["gdot"].numpy() - m["gdot"]).max() < 1e-10 * gmax
+    assert np.abs(fl["omega"].numpy() - m["omega"]).max() < 1e-9
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_c_and_torch_oracles_agree_on_small_aneurysm(q):
+    """Porous sac, Carreau-Yasuda, pulsatile Zou-He inlet, extrapolation outlet."""
+    prob = aneurysm_problem(24, q=q, small=True, u0=0.05, period=40.0)
+    _compare(prob, 25)
+
+
+def test_c_and_torch_oracles_agree_on_pipe():
+    _compare(pipe_problem(q=19), 15)
+
+
+def test_c_and_torch_oracles_agree_periodic_random_porosity():
+    rng = np.random.default_rng(3)
+    phi = (0.65 + 0.35 * rng.random((5, 4, 6))).astype(np.float32)
+    rheo = lattice_rheology(0.1, 0.01, 50.0, 0.4, 2.0)
+    prob = periodic_box_problem(6, 4, 5, q=27, rheology=rheo, body_force=(2e-4, -1e-4, 5e-5),
+                                obstacles=8, phi=phi, d_p=2.0)
+    _compare(prob, 20)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_zou_he_momentum_identity(q):
+    """After the inlet reconstruction every inlet cell carries
+    sum_i f_i c_i = rho (u_in - g/2), rho = sum_i f_i (phi = 1), with the
+    Hagen-Poiseuille profile u_in = 2 v(t) (1 - r^2/R^2) n (Sec. 4), from
+    arbitrary (perturbed) incoming populations."""
+    prob = aneurysm_problem(24, q=q, small=True, u0=0.04, amp=0.5, period=30.0)
+    o = Oracle(prob)
+    rng = np.random.default_rng(q)
+    f, om = o.get_state()
+    o.set_state(f * (1 + 0.1 * rng.standard_normal(f.shape)), om, 0)
+    t = 7
+    o.apply_boundaries(t)
+    f, _ = o.get_state()
+    c, w, _ = o.lattice()
+    cells = o.cells()
+    nx, ny, nz = prob.dims
+    b = prob.bc
+    v = b["u0"] * (1 + b["amp"] * math.sin(2 * math.pi * t / b["period"]))
+    n_in = 0
+    for k, idx in enumerate(cells):
+        if prob.flags.reshape(-1)[idx] != 2:
+            continue
+        n_in += 1
+        x, y = idx % nx, (idx // nx) % ny
+        r2 = (x + 0.5 - b["inlet_center"][0]) ** 2 + (y + 0.5 - b["inlet_center"][1]) ** 2
+        un = 2 * v * max(0.0, 1 - r2 / b["inlet_radius"] ** 2)
+        rho = f[k].sum()
+        mom = f[k] @ c
+        assert np.abs(mom - rho * np.array([0.0, 0.0, un])).max() < 1e-15
+    assert n_in > 20
+
+
+def test_reference_gradient_matches_finite_differences():
+    """d J / d phi from torch autograd (pull form) against central differences
+    (eps = 1e-4) of the C oracle's objective, J = time-and-sac mean of
+    rho |u|^2 / 2, at sac voxels with porosity strictly inside (0.6, 1)."""
+    prob = aneurysm_problem(24, q=27, small=True, u0=0.05, period=50.0)
+    T = 16
+    J, grad = TorchLBM(prob).gradient(prob.phi, T, prob.region)
+    J0 = Oracle(prob).run_objective(T, prob.region)
+    assert abs(J - J0) < 1e-13 * abs(J0)
+    rng = np.random.default_rng(1)
+    cand = np.argwhere((prob.region > 0) & (prob.flags > 0) & (prob.phi < 0.99) & (prob.phi > 0.61))
+    scale = np.abs(grad).max()
+    eps = 1e-4
+    for z, y, x in cand[rng.choice(len(cand), 5, replace=False)]:
+        ph = prob.phi.astype(np.float64).copy()
+        ph[z, y, x] += eps
+        jp = Oracle(prob, phi=ph).run_objective(T, prob.region)
+        ph[z, y, x] -= 2 * eps
+        jm = Oracle(prob, phi=ph).run_objective(T, prob.region)
+        fd = (jp - jm) / (2 * eps)
+        assert abs(fd - grad[z, y, x]) < 1e-4 * scale + 1e-6 * abs(fd)
