@@ -1,0 +1,377 @@
+"""Benchmark of the fused VANSE LBM step on GB300.
+
+Workload: the synthetic 384^3 aneurysm (D3Q27, Carreau-Yasuda blood, porous
+coil in the sac, pulsatile Zou-He inlet, pressure outlet), 1000 time steps per
+benchmark step, distributions stored as FP32; the FP16 and BF16 deviation
+storage variants are timed the same way and reported beside it with their
+velocity error against the FP64 oracle.
+
+One benchmark step = one 1000-time-step run of the workload.  The metric is
+fluid-cell lattice updates per second (MLUPS) and the fraction of the measured
+HBM copy bandwidth the step kernel reaches with its algorithmic bytes.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own replica on its own GPU (independent
+problems, no collective on the data path): weak scaling.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="aneurysm384", n=384, q=27, lbm_steps=1000, seed=0)
+METRIC = "fluid MLUPS and % of HBM roofline, FP32 vs FP16-stored at stated error"
+UNIT = "MLUPS"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def bytes_per_update(q, storage):
+    """Algorithmic bytes per fluid-cell update: read and write every
+    distribution once (2 Q s), read and write omega (8), read phi (4) and the
+    link mask (4)."""
+    s = 4 if storage == "f32" else 2
+    return 2 * q * s + 16
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2402_10809_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def load_traffic(storage):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
+    only if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("kernel_hash") != kernel_source_hash():
+        return None
+    v = d.get("per_launch_bytes", {}).get(f"{WORKLOAD['name']}_{storage}")
+    return v
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        backend = "nccl"
+        dist.init_process_group(backend)
+        return ws, rank, local, dist
+    return 1, 0, 0, None
+
+
+def flush_l2(torch, buf):
+    buf.fill_(1.0)
+
+
+def time_variant(torch, lbm, prob, storage, steps, warmup, lbm_steps, flush):
+    sim = lbm.Simulation(prob, storage=storage)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush_l2(torch, flush)
+        sim.step(lbm_steps)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush_l2(torch, flush)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(lbm_steps)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return sim, times
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local, dist = dist_setup()
+    torch.cuda.set_device(local)
+    from lbm_inputs import aneurysm_problem
+    from paper_2402_10809_gb300 import lbm
+
+    lbm.load()
+    prob = aneurysm_problem(WORKLOAD["n"], q=WORKLOAD["q"], seed=WORKLOAD["seed"])
+    nf = prob.n_fluid
+    L = args.lbm_steps
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    peak, peak_kind = load_peaks()
+
+    # ---- timed region: FP32 storage (the headline), barrier + sync on both sides
+    sim, _ = time_variant(torch, lbm, prob, "f32", 0, args.warmup, L, flush)
+    for _ in range(args.warmup):
+        flush_l2(torch, flush)
+        sim.step(L)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    per = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush_l2(torch, flush)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(L)
+            e1.record(stream)
+            e1.synchronize()
+            per.append(e0.elapsed_time(e1) / 1e3)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total = sum(per)
+    if dist:
+        t = torch.tensor([total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    clocks = clk.summary()
+    launch_s = total / (args.steps * L)  # average step-kernel launch duration (back-to-back launches)
+    mlups = ws * nf * L * args.steps / total / 1e6
+    bpu = bytes_per_update(WORKLOAD["q"], "f32")
+    achieved = bpu * nf / launch_s / 1e9
+    traffic = load_traffic("f32")
+
+    # ---- storage variants, same protocol
+    variants = {}
+    for st in ("f16dev", "bf16dev"):
+        s2, tv = time_variant(torch, lbm, prob, st, max(3, args.steps // 2), args.warmup, L, flush)
+        tv_mean = sum(tv) / len(tv)
+        b2 = bytes_per_update(WORKLOAD["q"], st)
+        variants[st] = {"value": nf * L / tv_mean / 1e6, "unit": UNIT,
+                        "roofline_frac": b2 * nf / (tv_mean / L) / 1e9 / peak,
+                        "bytes_per_update": b2, "traffic": load_traffic(st)}
+        s2.close()
+
+    # ---- end to end through the C ABI with host buffers (pinned), per step:
+    # H2D of flags + porosity + region, set-up, L time steps, D2H of diagnostics
+    e2e = None
+    if not args.no_e2e:
+        pin_flags = torch.from_numpy(np.ascontiguousarray(prob.flags)).pin_memory()
+        pin_phi = torch.from_numpy(np.ascontiguousarray(prob.phi)).pin_memory()
+        pin_reg = torch.from_numpy(np.ascontiguousarray(prob.region)).pin_memory()
+        grid = lbm.make_grid(prob.dims, prob.q, "f32", prob.periodic)
+        r, p, b = lbm.make_params(prob.rheology, prob.porous, prob.bc)
+        nbytes = lbm.lbm_workspace_size(grid, nf)
+        wsb = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        sh = stream.cuda_stream
+
+        def e2e_step():
+            ctx = lbm.lbm_init(grid, pin_flags.data_ptr(), pin_phi.data_ptr(), 0, r, p, b, wsb.data_ptr(), nbytes, sh)
+            lbm.lbm_step(ctx, L)
+            d = lbm.lbm_diag(ctx, pin_reg.data_ptr(), 0)
+            lbm.lbm_destroy(ctx)
+            return d
+
+        for _ in range(max(1, args.warmup // 2)):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ne = max(2, args.steps // 2)
+        for _ in range(ne):
+            flush_l2(torch, flush)
+            e2e_step()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": nf * L * ne / te / 1e6 * ws, "unit": UNIT,
+               "h2d_bytes_per_step": int(prob.flags.nbytes + prob.phi.nbytes + prob.region.nbytes),
+               "d2h_bytes_per_step": 64}
+
+    line = {
+        "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD['name']} D3Q27 FP32-stored, {L} time steps per step, "
+                               f"{nf} fluid cells, Carreau-Yasuda, porous sac, pulsatile inlet",
+                   "box": [WORKLOAD["n"]] * 3, "fluid_cells": nf, "time_steps_per_step": L,
+                   "q": WORKLOAD["q"], "storage": "f32", "parallelism": f"replicas{ws}",
+                   "l2": "inputs larger than L2 (412 MB touched per time step) and a 256 MB L2 flush "
+                         "before each timed step"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "bytes_per_update": bpu,
+                     "kernel": "lbm_kernel<27,float,step> average over back-to-back launches"},
+        "storage_variants": variants,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": args.steps * L,
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(prob, sim_factory=lambda st: lbm.Simulation(prob, storage=st),
+                                            sample_steps=args.cpu_sample_steps)
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(prob, sim_factory=None, sample_steps=40):
+    """The FP64 oracle timed on the host cores on a bounded sample (the first
+    sample_steps time steps of the same workload).  When a GPU factory is given,
+    the GPU state after the same steps is compared with it for each storage."""
+    from oracle.oracle import Oracle, num_threads
+
+    o = Oracle(prob)
+    t0 = time.perf_counter()
+    o.step(sample_steps)
+    dt = time.perf_counter() - t0
+    out = {"value": prob.n_fluid * sample_steps / dt / 1e6, "unit": UNIT, "cores": num_threads(),
+           "kind": "oracle",
+           "sample": f"first {sample_steps} time steps of {WORKLOAD['name']} (D3Q27), FP64, OpenMP"}
+    if sim_factory is not None:
+        r = o.moments()
+        fl = prob.flags > 0
+        errs = {}
+        for st in ("f32", "f16dev", "bf16dev"):
+            s = sim_factory(st)
+            s.step(sample_steps)
+            g = s.moments()
+            den = np.abs(r["u"][:, fl]).max()
+            gd = np.abs(r["gdot"][fl]).max()
+            errs[st] = {"u_max_rel": float(np.abs(g["u"][:, fl] - r["u"][:, fl]).max() / den),
+                        "gdot_max_rel": float(np.abs(g["gdot"][fl] - r["gdot"][fl]).max() / gd),
+                        "after_steps": sample_steps}
+            s.close()
+        out["error_vs_oracle"] = errs
+    return out
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from lbm_inputs import aneurysm_problem
+    from oracle.oracle import Oracle, num_threads
+
+    prob = aneurysm_problem(WORKLOAD["n"], q=WORKLOAD["q"], seed=WORKLOAD["seed"])
+    nf = prob.n_fluid
+    o = Oracle(prob)
+    per = args.ref_sample_steps
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(per)
+    dt = time.perf_counter() - t0
+    v = nf * per * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD['name']} D3Q27, each step a bounded sample of {per} time steps",
+                       "box": [WORKLOAD["n"]] * 3, "fluid_cells": nf, "q": WORKLOAD["q"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": num_threads(), "kind": "oracle",
+                             "sample": f"{per} time steps per step of {WORKLOAD['name']}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lbm-steps", type=int, default=WORKLOAD["lbm_steps"])
+    ap.add_argument("--cpu-sample-steps", type=int, default=30)
+    ap.add_argument("--ref-sample-steps", type=int, default=4)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: warm-up raised to 3 (timing rule)", file=sys.stderr)
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

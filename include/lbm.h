@@ -1,0 +1,164 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann solver for the
+ * volume-averaged Navier-Stokes equations (VANSE) with Carreau-Yasuda blood
+ * rheology and a coil represented as a porous medium, after
+ * M. Horvat, S. B. Lunowa, D. Sytnyk, B. Wohlmuth, "A Lattice Boltzmann Method
+ * for Non-Newtonian Blood Flow in Coiled Intracranial Aneurysms",
+ * arXiv 2402.10809 (the "paper" below).
+ *
+ * Conventions shared by every call
+ *  - Grid arrays are dense, x fastest: cell index = x + nx * (y + ny * z).
+ *  - Lattice units inside: dx = dt = 1, c_s^2 = 1/3; physical parameters are
+ *    converted with the spacing, time step and reference density of Table 1.
+ *  - Memory: the library never allocates device memory.  The caller passes one
+ *    device workspace of at least lbm_workspace_size() bytes, 256-byte
+ *    aligned, and keeps it alive until lbm_destroy().  The context itself is a
+ *    small host object.  All work is enqueued on the caller's CUDA stream;
+ *    calls that return host data synchronise that stream.
+ *  - Errors: every call returns an lbm_status; lbm_last_error() gives a text.
+ *    No call aborts, traps or asserts on the device.
+ *  - One context serves one stream; calls on one context must not overlap.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,    /* bad argument, size or geometry */
+    LBM_ENOMEM = 2,    /* workspace or destination too small */
+    LBM_ECUDA = 3,     /* a CUDA runtime call failed (text in lbm_last_error) */
+    LBM_EUNSTABLE = 4, /* non-finite state detected by the periodic check */
+    LBM_ESTATE = 5     /* call not valid in the current state */
+} lbm_status;
+
+/* Cell flags (uint8). */
+enum { LBM_SOLID = 0, LBM_FLUID = 1, LBM_INLET = 2, LBM_OUTLET = 3 };
+
+/* Storage of the particle densities f_i in HBM.  All arithmetic is FP32.
+ * F32:      f_i - w_i phi_hat stored as float;
+ * F16DEV:   the same deviation stored as IEEE binary16 (round to nearest even);
+ * BF16DEV:  the same deviation stored as bfloat16 (round to nearest even).
+ * phi_hat is the porosity of the cell the value streams to (the cell's own
+ * porosity where that neighbour is solid or outside), so a value is always
+ * decoded with the porosity of the cell that reads it. */
+enum { LBM_F32 = 0, LBM_F16DEV = 1, LBM_BF16DEV = 2 };
+
+typedef struct {
+    int32_t nx, ny, nz;    /* box size, each 2..1024 */
+    int32_t q;             /* velocity set: 27 (the paper's D3Q27, Sec. 3) or 19 */
+    int32_t storage;       /* LBM_F32, LBM_F16DEV or LBM_BF16DEV */
+    int32_t periodic[3];   /* 1: axis wraps around */
+} lbm_grid;
+
+/* Carreau-Yasuda law, Eq. (3): mu(g) = mu_inf + (mu0 - mu_inf)(1 + (lambda g)^a)^((n-1)/a),
+ * in SI units; rho0 [kg/m^3], dx [m], dt [s] map them to the lattice (Table 1):
+ * nu_lattice = mu / rho0 * dt / dx^2, lambda_lattice = lambda / dt.
+ * Pass rho0 = dx = dt = 1 to give lattice values directly. */
+typedef struct {
+    double mu0, mu_inf, lambda, n, a;
+    double rho0, dx, dt;
+} lbm_rheology;
+
+/* Darcy-Forchheimer drag of Sec. 2, f(u) = -phi^2 nu u / k - phi^3 C_F |u| u / sqrt(k),
+ * with Kozeny-Carman k = phi^3 d_p^2 / (150 (1 - phi)^2) and Ergun
+ * C_F = 1.75 / sqrt(150 phi^3).  d_p [m]; k_const [m^2] > 0 replaces
+ * Kozeny-Carman by a constant permeability (acting where phi < 1);
+ * nu_darcy [m^2/s] <= 0 selects nu = mu0 / rho0 (Sec. 4); forchheimer 0/1. */
+typedef struct {
+    double d_p, k_const, nu_darcy;
+    int32_t forchheimer;
+} lbm_porous;
+
+/* Forcing and open boundaries (Sec. 4).  body_force: per unit mass, lattice units.
+ * Inlet (Zou-He velocity inlet): cells flagged LBM_INLET on the face
+ * inlet_axis (0 x, 1 y, 2 z), inlet_side (0 low, 1 high); Hagen-Poiseuille
+ * profile u_perp = 2 v(t) max(0, 1 - r^2 / R^2) with r measured from
+ * inlet_center (lattice coordinates, cell centres at integer + 1/2) and
+ * R = inlet_radius; mean velocity v(t) = u0 (1 + amp sin(2 pi t / period)),
+ * ramped linearly over the first ramp_steps steps when ramp_steps > 0.
+ * Outlet: cells flagged LBM_OUTLET on the face outlet_axis / outlet_side,
+ * non-equilibrium extrapolation from the first interior neighbour with the
+ * prescribed density rho_out.  An axis of -1 disables that boundary. */
+typedef struct {
+    double body_force[3];
+    int32_t inlet_axis, inlet_side;
+    double inlet_center[3];
+    double inlet_radius, u0, amp, period, ramp_steps;
+    int32_t outlet_axis, outlet_side;
+    double rho_out;
+} lbm_bc;
+
+/* Bytes of device workspace for a grid holding n_fluid non-solid cells
+ * (pass n_fluid < 0 for the bound n_fluid = nx*ny*nz).  0 on a bad grid. */
+size_t lbm_workspace_size(const lbm_grid* grid, int64_t n_fluid);
+
+/* Creates a context and sets the initial state (Sec. 3, Sec. 4):
+ * f_i = f_i^eq(rho = 1, u = 0) = w_i phi, omega = omega(mu0) at rho = 1, and
+ * the inlet / outlet reconstruction of time 0 is applied by the first step.
+ *  flags     [nz][ny][nx] uint8 LBM_SOLID / FLUID / INLET / OUTLET;
+ *  porosity  [nz][ny][nx] float, phi in (0, 1]; phi must be 1 on inlet and
+ *            outlet cells and on each outlet cell's interior neighbour, which
+ *            must be LBM_FLUID;
+ *  inputs_on_device: 1 if flags / porosity are device pointers, 0 for host;
+ *  workspace / workspace_bytes: caller-owned device memory (see above);
+ *  stream: a cudaStream_t (NULL = legacy default stream).
+ * The inputs are copied into the workspace; the caller may free them after
+ * this call returns.  Returns LBM_EINVAL on bad sizes, flags or porosity. */
+lbm_status lbm_init(lbm_ctx** ctx, const lbm_grid* grid, const uint8_t* flags, const float* porosity,
+                    int32_t inputs_on_device, const lbm_rheology* rheology, const lbm_porous* porous,
+                    const lbm_bc* bc, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Advances n >= 0 time steps (Sec. 3): each step pulls f(t) from the neighbours
+ * (half-way bounce-back at walls, Zou-He inlet, extrapolation outlet), computes
+ * rho, u (explicit Darcy-Forchheimer velocity), the force, Pi, the shear rate
+ * gdot = omega(t-1) ||Pi||_F / (c_s^2 rho), mu(gdot) and omega(t), collides
+ * with Omega^phi + Omega^f + Omega^SRT and stores f*(t).  Asynchronous. */
+lbm_status lbm_step(lbm_ctx* ctx, int32_t n);
+
+/* Fields of the current time t on the dense box (0 at solid cells):
+ * rho [N], u [3][N] (x, y, z planes), shear_rate gdot(t) [N], omega(t) [N].
+ * Any pointer may be NULL.  dst_on_device: 1 device pointers (asynchronous),
+ * 0 host pointers (synchronises the stream). */
+lbm_status lbm_moments(lbm_ctx* ctx, float* rho, float* u, float* shear_rate, float* omega,
+                       int32_t dst_on_device);
+
+/* Diagnostics of the current time, accumulated in FP64 (sac averages of the
+ * paper's Sec. 4 results among them): out[0] mass sum_x sum_i f_i,
+ * out[1] kinetic energy sum rho |u|^2 / 2, out[2] sum of |u| over the region,
+ * out[3] number of region cells, out[4] max |u|, out[5] min omega,
+ * out[6] max omega, out[7] number of non-finite cells.  region: [N] uint8
+ * (nonzero = in the region) or NULL for an empty region; region_on_device
+ * tells where it lives.  out is host memory; the call synchronises. */
+lbm_status lbm_diag(lbm_ctx* ctx, const uint8_t* region, int32_t region_on_device, double out[8]);
+
+/* Every check_every steps of later lbm_step calls, run the non-finite count of
+ * lbm_diag and return LBM_EUNSTABLE when it is nonzero (0 = never, default). */
+lbm_status lbm_set_check(lbm_ctx* ctx, int32_t check_every);
+
+/* Checkpoint of the full state (distributions, relaxation rates, time): size in
+ * bytes, save into / load from caller memory (host or device). */
+size_t lbm_state_size(const lbm_ctx* ctx);
+lbm_status lbm_save(lbm_ctx* ctx, void* dst, size_t bytes, int32_t dst_on_device);
+lbm_status lbm_load(lbm_ctx* ctx, const void* src, size_t bytes, int32_t src_on_device);
+
+/* Current time step, number of non-solid cells, and the last error text. */
+int64_t lbm_time(const lbm_ctx* ctx);
+int64_t lbm_fluid_count(const lbm_ctx* ctx);
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Releases the host context (the workspace stays the caller's). */
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

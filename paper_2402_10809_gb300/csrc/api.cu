@@ -1,0 +1,520 @@
+// Host side of the C ABI declared in include/lbm.h: workspace layout, input
+// validation, unit conversion (Table 1 scales), set-up and the launches of the
+// fused step, moments and diagnostics kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "lbm.h"
+#include "setup.cuh"
+
+namespace lbm {
+cudaError_t launch_step_19_f32(int, const Params&, cudaStream_t);
+cudaError_t launch_step_19_f16(int, const Params&, cudaStream_t);
+cudaError_t launch_step_19_bf16(int, const Params&, cudaStream_t);
+cudaError_t launch_step_27_f32(int, const Params&, cudaStream_t);
+cudaError_t launch_step_27_f16(int, const Params&, cudaStream_t);
+cudaError_t launch_step_27_bf16(int, const Params&, cudaStream_t);
+}  // namespace lbm
+
+using namespace lbm;
+
+namespace {
+
+constexpr uint64_t kStateMagic = 0x314d425356414e45ull;  // checkpoint header tag
+constexpr size_t kHeader = 256;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t elem_size(int storage) { return storage == LBM_F32 ? 4 : 2; }
+
+struct Layout {
+    size_t f[2], phi, flags, region, counts, offsets, totals, err, diag_out;
+    size_t cells, mask, omega, bnd_prof, bnd_nbmask, partials, staging, pack, end;
+    size_t fixed_end;
+};
+
+bool grid_ok(const lbm_grid* g)
+{
+    if (!g) return false;
+    if (g->q != 19 && g->q != 27) return false;
+    if (g->storage < LBM_F32 || g->storage > LBM_BF16DEV) return false;
+    const int n[3] = {g->nx, g->ny, g->nz};
+    for (int a = 0; a < 3; ++a)
+        if (n[a] < 2 || n[a] > 1024) return false;
+    return true;
+}
+
+Layout layout(const lbm_grid* g, long long nf)
+{
+    Layout L{};
+    const long long N = (long long)g->nx * g->ny * g->nz;
+    const size_t fb = (size_t)g->q * (size_t)N * elem_size(g->storage);
+    const long long nblk = (N + kSetupChunk - 1) / kSetupChunk;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    L.f[0] = take(fb);
+    L.f[1] = take(fb);
+    L.phi = take((size_t)N * 4);
+    L.flags = take((size_t)N);
+    L.region = take((size_t)N);
+    L.counts = take((size_t)nblk * 3 * 4);
+    L.offsets = take((size_t)nblk * 3 * 4);
+    L.totals = take(16);
+    L.err = take(32);
+    L.diag_out = take(8 * 8);
+    L.fixed_end = o;
+    const size_t n = (size_t)(nf > 0 ? nf : 1);
+    L.cells = take(n * 4);
+    L.mask = take(n * 4);
+    L.omega = take(n * 4);
+    L.bnd_prof = take(n * 4);
+    L.bnd_nbmask = take(n * 4);
+    L.partials = take(((n + kBlock - 1) / kBlock) * kDiagSlots * 8);
+    L.staging = take(n * 6 * 4);
+    L.pack = take(n * ((size_t)g->q * elem_size(g->storage) + 4));
+    L.end = o;
+    return L;
+}
+
+cudaError_t launch(const lbm_grid& g, int mode, const Params& P, cudaStream_t s)
+{
+    if (g.q == 19) {
+        if (g.storage == LBM_F32) return launch_step_19_f32(mode, P, s);
+        if (g.storage == LBM_F16DEV) return launch_step_19_f16(mode, P, s);
+        return launch_step_19_bf16(mode, P, s);
+    }
+    if (g.storage == LBM_F32) return launch_step_27_f32(mode, P, s);
+    if (g.storage == LBM_F16DEV) return launch_step_27_f16(mode, P, s);
+    return launch_step_27_bf16(mode, P, s);
+}
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_grid grid{};
+    lbm_rheology rheo{};
+    lbm_porous por{};
+    lbm_bc bc{};
+    cudaStream_t stream = nullptr;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    Layout L{};
+    long long N = 0;
+    int n_cells = 0, n_bulk = 0, n_in = 0, n_out = 0;
+    int cur = 0;
+    long long t = 0;
+    int check_every = 0;
+    bool ready = false;  // set once lbm_init has fully succeeded
+    long long since_check = 0;
+    float omega0 = 1.0f;
+    Params base{};
+    std::vector<uint32_t> host_cells;
+    std::string err;
+
+    template <class T>
+    T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+    void* f(int k) const { return ws + L.f[k]; }
+};
+
+static lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+static lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where)
+{
+    return fail(c, LBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(call, where)                    \
+    do {                                         \
+        cudaError_t e_ = (call);                 \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+extern "C" size_t lbm_workspace_size(const lbm_grid* grid, int64_t n_fluid)
+{
+    if (!grid_ok(grid)) return 0;
+    const long long N = (long long)grid->nx * grid->ny * grid->nz;
+    return layout(grid, n_fluid < 0 ? N : (n_fluid > N ? N : n_fluid)).end;
+}
+
+static lbm_status run_diag(lbm_ctx* c, const uint8_t* region_dev, double out[8])
+{
+    Params P = c->base;
+    P.fsrc = c->f(c->cur);
+    P.fdst = nullptr;
+    P.t = c->t;
+    P.region = region_dev;
+    P.partials = c->at<double>(c->L.partials);
+    LBM_CUDA(launch(c->grid, kModeDiag, P, c->stream), "diag kernel");
+    const int nblk = (c->n_cells + kBlock - 1) / kBlock;
+    double* dout = c->at<double>(c->L.diag_out);
+    if (nblk > 0) {
+        LBM_CUDA(launch_diag_finish(P.partials, nblk, dout, c->stream), "diag reduction");
+        LBM_CUDA(cudaMemcpyAsync(out, dout, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "diag copy");
+        LBM_CUDA(cudaStreamSynchronize(c->stream), "diag sync");
+    } else {
+        for (int k = 0; k < 8; ++k) out[k] = 0.0;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_t* flags, const float* porosity,
+                               int32_t inputs_on_device, const lbm_rheology* rheo, const lbm_porous* por,
+                               const lbm_bc* bc, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ENOMEM;
+    *out = c;
+    if (!grid_ok(grid)) return fail(c, LBM_EINVAL, "grid: q must be 19 or 27, storage 0..2, sizes 2..1024");
+    if (!flags || !porosity || !rheo || !por || !bc || !workspace)
+        return fail(c, LBM_EINVAL, "null input pointer");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(c, LBM_EINVAL, "workspace not 256-byte aligned");
+    if (!(rheo->mu0 > 0 && rheo->mu_inf > 0 && rheo->rho0 > 0 && rheo->dx > 0 && rheo->dt > 0 && rheo->a > 0 &&
+          rheo->lambda >= 0))
+        return fail(c, LBM_EINVAL, "rheology: mu0, mu_inf, rho0, dx, dt, a must be > 0 and lambda >= 0");
+    if (!(por->k_const > 0) && !(por->d_p > 0)) return fail(c, LBM_EINVAL, "porous: d_p must be > 0 (or k_const > 0)");
+    if (bc->inlet_axis < -1 || bc->inlet_axis > 2 || bc->outlet_axis < -1 || bc->outlet_axis > 2)
+        return fail(c, LBM_EINVAL, "bc: axes must be -1, 0, 1 or 2");
+    if (bc->inlet_axis >= 0 && !(bc->period > 0 && bc->inlet_radius > 0))
+        return fail(c, LBM_EINVAL, "bc: inlet needs period > 0 and inlet_radius > 0");
+    if (bc->outlet_axis >= 0 && !(bc->rho_out > 0)) return fail(c, LBM_EINVAL, "bc: rho_out must be > 0");
+    c->grid = *grid;
+    c->rheo = *rheo;
+    c->por = *por;
+    c->bc = *bc;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->ws = static_cast<char*>(workspace);
+    c->ws_bytes = workspace_bytes;
+    c->N = (long long)grid->nx * grid->ny * grid->nz;
+    c->L = layout(grid, 0);
+    if (workspace_bytes < c->L.end) return fail(c, LBM_ENOMEM, "workspace smaller than lbm_workspace_size(grid, 0)");
+
+    const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    LBM_CUDA(cudaMemcpyAsync(c->at<uint8_t>(c->L.flags), flags, (size_t)c->N, kind, c->stream), "copy flags");
+    LBM_CUDA(cudaMemcpyAsync(c->at<float>(c->L.phi), porosity, (size_t)c->N * 4, kind, c->stream), "copy porosity");
+
+    // cell list: count, scan, emit
+    LBM_CUDA(launch_setup_cells(c->at<uint8_t>(c->L.flags), c->N, grid->nx, grid->ny, c->at<uint32_t>(c->L.counts),
+                                c->at<uint32_t>(c->L.offsets), c->at<uint32_t>(c->L.totals), c->stream, 0, nullptr),
+             "setup count");
+    uint32_t tot[3] = {0, 0, 0};
+    LBM_CUDA(cudaMemcpyAsync(tot, c->at<uint32_t>(c->L.totals), sizeof(tot), cudaMemcpyDeviceToHost, c->stream),
+             "copy totals");
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "setup sync");
+    c->n_bulk = (int)tot[0];
+    c->n_in = (int)tot[1];
+    c->n_out = (int)tot[2];
+    c->n_cells = c->n_bulk + c->n_in + c->n_out;
+    c->L = layout(grid, c->n_cells);
+    if (workspace_bytes < c->L.end)
+        return fail(c, LBM_ENOMEM, "workspace smaller than lbm_workspace_size(grid, " + std::to_string(c->n_cells) + ")");
+    LBM_CUDA(launch_setup_cells(c->at<uint8_t>(c->L.flags), c->N, grid->nx, grid->ny, c->at<uint32_t>(c->L.counts),
+                                c->at<uint32_t>(c->L.offsets), c->at<uint32_t>(c->L.totals), c->stream, 1,
+                                c->at<uint32_t>(c->L.cells)),
+             "setup emit");
+
+    SetupParams S{};
+    S.nx = grid->nx;
+    S.ny = grid->ny;
+    S.nz = grid->nz;
+    for (int a = 0; a < 3; ++a) S.periodic[a] = grid->periodic[a] ? 1 : 0;
+    S.n_cells = c->n_cells;
+    S.n_bulk = c->n_bulk;
+    S.flags = c->at<uint8_t>(c->L.flags);
+    S.phi = c->at<float>(c->L.phi);
+    S.cells = c->at<uint32_t>(c->L.cells);
+    S.mask = c->at<uint32_t>(c->L.mask);
+    S.bnd_prof = c->at<float>(c->L.bnd_prof);
+    S.bnd_nbmask = c->at<uint32_t>(c->L.bnd_nbmask);
+    S.in_axis = bc->inlet_axis;
+    S.in_side = bc->inlet_side;
+    S.out_axis = bc->outlet_axis;
+    S.out_side = bc->outlet_side;
+    for (int a = 0; a < 3; ++a) S.in_center[a] = bc->inlet_center[a];
+    S.in_radius = bc->inlet_radius;
+    S.err = c->at<uint32_t>(c->L.err);
+    LBM_CUDA(cudaMemsetAsync(S.err, 0, 32, c->stream), "clear error words");
+    LBM_CUDA(launch_setup_mask(grid->q, S, c->stream), "setup_mask");
+    uint32_t errv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    LBM_CUDA(cudaMemcpyAsync(errv, S.err, 32, cudaMemcpyDeviceToHost, c->stream), "copy error words");
+    c->host_cells.resize(c->n_cells);
+    if (c->n_cells > 0)
+        LBM_CUDA(cudaMemcpyAsync(c->host_cells.data(), S.cells, (size_t)c->n_cells * 4, cudaMemcpyDeviceToHost,
+                                 c->stream), "copy cell list");
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "setup sync");
+    const uint32_t errw = errv[0];
+    if (errw) {
+        float bad_phi;
+        std::memcpy(&bad_phi, &errv[3], 4);
+        char where[256];
+        const uint32_t why = errv[4];
+        std::snprintf(where, sizeof(where), " (first at cell x=%u y=%u z=%u, porosity %.9g%s%s%s%s)",
+                      errv[2] & 1023u, (errv[2] >> 10) & 1023u, errv[2] >> 20, (double)bad_phi,
+                      (why & 1u) ? "; no inlet axis" : "", (why & 2u) ? "; inlet axis is periodic" : "",
+                      (why & 4u) ? "; not on the inlet face" : "", (why & 8u) ? "; porosity is not 1" : "");
+        if (errw & kErrPorosity)
+            return fail(c, LBM_EINVAL, std::string("porosity must lie in (0, 1] on every non-solid cell") + where);
+        if (errw & kErrInlet)
+            return fail(c, LBM_EINVAL,
+                        std::string("inlet cells must lie on the inlet face, with an inlet configured and porosity 1") +
+                            where);
+        return fail(c, LBM_EINVAL,
+                    std::string("outlet cells must lie on the outlet face with porosity 1 and a fluid interior "
+                                "neighbour of porosity 1") + where);
+    }
+
+    // Lattice units from the Table 1 scales (Sec. 4): nu = mu / rho0 * dt / dx^2.
+    const double scale = rheo->dt / (rheo->dx * rheo->dx);
+    const double mu0 = rheo->mu0 / rheo->rho0 * scale;
+    const double mui = rheo->mu_inf / rheo->rho0 * scale;
+    const double nu_d = por->nu_darcy > 0 ? por->nu_darcy * scale : mu0;  // nu = mu0 / rho0 (Sec. 4)
+    Params& P = c->base;
+    P.nx = grid->nx;
+    P.ny = grid->ny;
+    P.nz = grid->nz;
+    P.N = c->N;
+    P.n_cells = c->n_cells;
+    P.n_bulk = c->n_bulk;
+    P.cells = S.cells;
+    P.mask = S.mask;
+    P.phi = S.phi;
+    P.bnd_prof = S.bnd_prof;
+    P.bnd_nbmask = S.bnd_nbmask;
+    P.gx = (float)bc->body_force[0];
+    P.gy = (float)bc->body_force[1];
+    P.gz = (float)bc->body_force[2];
+    if (por->k_const > 0) {
+        const double kc = por->k_const / (rheo->dx * rheo->dx);
+        P.drag_kc = 0;
+        P.drag_a = (float)(nu_d / kc);
+        P.drag_b = por->forchheimer ? (float)(1.75 / std::sqrt(150.0 * kc)) : 0.0f;
+    } else {
+        const double d = por->d_p / rheo->dx;
+        P.drag_kc = 1;
+        P.drag_a = (float)(150.0 * nu_d / (d * d));
+        P.drag_b = por->forchheimer ? (float)(1.75 / d) : 0.0f;
+    }
+    P.mu0 = (float)mu0;
+    P.mu_inf = (float)mui;
+    P.lam = (float)(rheo->lambda / rheo->dt);
+    P.cy_a = (float)rheo->a;
+    P.cy_e = (float)((rheo->n - 1.0) / rheo->a);
+    P.cy_a_two = rheo->a == 2.0 ? 1 : 0;
+    P.in_axis = bc->inlet_axis;
+    P.in_side = bc->inlet_side;
+    P.out_axis = bc->outlet_axis;
+    P.out_side = bc->outlet_side;
+    P.u0 = bc->u0;
+    P.amp = bc->amp;
+    P.period = bc->period > 0 ? bc->period : 1.0;
+    P.ramp = bc->ramp_steps;
+    P.rho_out = (float)bc->rho_out;
+    P.omega = c->at<float>(c->L.omega);
+    c->omega0 = (float)(2.0 / (6.0 * mu0 + 1.0));  // omega(mu0) at rho = 1
+
+    // initial state: rest equilibrium (zero deviations)
+    LBM_CUDA(launch_init_state(grid->storage, S.cells, c->n_cells, grid->nx, grid->ny, c->N, grid->q, c->f(0), P.omega,
+                               c->omega0, c->stream),
+             "init_state");
+    c->cur = 0;
+    c->t = 0;
+    c->ready = true;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_step(lbm_ctx* c, int32_t n)
+{
+    if (!c) return LBM_EINVAL;
+    if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    for (int32_t s = 0; s < n; ++s) {
+        Params P = c->base;
+        P.fsrc = c->f(c->cur);
+        P.fdst = c->f(1 - c->cur);
+        P.t = c->t;
+        LBM_CUDA(launch(c->grid, kModeStep, P, c->stream), "step kernel");
+        c->cur ^= 1;
+        c->t += 1;
+        if (c->check_every > 0 && ++c->since_check >= c->check_every) {
+            c->since_check = 0;
+            double d[8];
+            lbm_status st = run_diag(c, nullptr, d);
+            if (st != LBM_OK) return st;
+            if (d[7] > 0) return fail(c, LBM_EUNSTABLE, "non-finite state at step " + std::to_string(c->t));
+        }
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho, float* u, float* shear_rate, float* omega,
+                                  int32_t dst_on_device)
+{
+    if (!c) return LBM_EINVAL;
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    Params P = c->base;
+    P.fsrc = c->f(c->cur);
+    P.fdst = nullptr;
+    P.t = c->t;
+    const size_t N = (size_t)c->N;
+    if (dst_on_device) {
+        float* outs[6] = {rho, u, u ? u + N : nullptr, u ? u + 2 * N : nullptr, shear_rate, omega};
+        for (float* o : outs)
+            if (o) LBM_CUDA(cudaMemsetAsync(o, 0, N * 4, c->stream), "clear moments");
+        P.o_rho = outs[0];
+        P.o_ux = outs[1];
+        P.o_uy = outs[2];
+        P.o_uz = outs[3];
+        P.o_gdot = outs[4];
+        P.o_omega = outs[5];
+        P.o_compact = 0;
+        return launch(c->grid, kModeMoments, P, c->stream) == cudaSuccess ? LBM_OK
+                                                                          : fail(c, LBM_ECUDA, "moments kernel");
+    }
+    const size_t n = (size_t)c->n_cells;
+    float* st = c->at<float>(c->L.staging);
+    P.o_rho = st;
+    P.o_ux = st + n;
+    P.o_uy = st + 2 * n;
+    P.o_uz = st + 3 * n;
+    P.o_gdot = st + 4 * n;
+    P.o_omega = st + 5 * n;
+    P.o_compact = 1;
+    std::vector<float> h(6 * n);
+    if (n > 0) {
+        LBM_CUDA(launch(c->grid, kModeMoments, P, c->stream), "moments kernel");
+        LBM_CUDA(cudaMemcpyAsync(h.data(), st, 6 * n * 4, cudaMemcpyDeviceToHost, c->stream), "moments copy");
+    }
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "moments sync");
+    float* outs[6] = {rho, u, u ? u + N : nullptr, u ? u + 2 * N : nullptr, shear_rate, omega};
+    const long long plane = (long long)c->grid.nx * c->grid.ny;
+    for (int k = 0; k < 6; ++k) {
+        if (!outs[k]) continue;
+        std::memset(outs[k], 0, N * 4);
+        for (size_t p = 0; p < n; ++p) {
+            const uint32_t pc = c->host_cells[p];
+            const long long idx = (pc & 1023u) + (long long)c->grid.nx * ((pc >> 10) & 1023u) + plane * (pc >> 20);
+            outs[k][idx] = h[k * n + p];
+        }
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_diag(lbm_ctx* c, const uint8_t* region, int32_t region_on_device, double out[8])
+{
+    if (!c || !out) return LBM_EINVAL;
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    const uint8_t* reg = nullptr;
+    if (region) {
+        if (region_on_device) {
+            reg = region;
+        } else {
+            LBM_CUDA(cudaMemcpyAsync(c->at<uint8_t>(c->L.region), region, (size_t)c->N, cudaMemcpyHostToDevice,
+                                     c->stream), "copy region");
+            reg = c->at<uint8_t>(c->L.region);
+        }
+    }
+    return run_diag(c, reg, out);
+}
+
+extern "C" lbm_status lbm_set_check(lbm_ctx* c, int32_t check_every)
+{
+    if (!c) return LBM_EINVAL;
+    if (check_every < 0) return fail(c, LBM_EINVAL, "check_every must be >= 0");
+    c->check_every = check_every;
+    c->since_check = 0;
+    return LBM_OK;
+}
+
+namespace {
+struct StateHeader {
+    uint64_t magic;
+    int64_t t;
+    int64_t n_cells;
+    int32_t q, storage;
+};
+}  // namespace
+
+extern "C" size_t lbm_state_size(const lbm_ctx* c)
+{
+    if (!c || !c->ready) return 0;
+    return kHeader + (size_t)c->n_cells * ((size_t)c->grid.q * elem_size(c->grid.storage) + 4);
+}
+
+static lbm_status pack(lbm_ctx* c, int unpack, void* state)
+{
+    const lbm_grid& G = c->grid;
+    LBM_CUDA(launch_pack_state(G.storage, c->at<uint32_t>(c->L.cells), c->n_cells, G.nx, G.ny, c->N, G.q,
+                               c->f(c->cur), state, unpack, c->stream),
+             "pack_state");
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_save(lbm_ctx* c, void* dst, size_t bytes, int32_t dst_on_device)
+{
+    if (!c || !dst) return LBM_EINVAL;
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    const size_t need = lbm_state_size(c);
+    if (bytes < need) return fail(c, LBM_ENOMEM, "destination smaller than lbm_state_size");
+    StateHeader h{kStateMagic, c->t, c->n_cells, c->grid.q, c->grid.storage};
+    char* pk = c->at<char>(c->L.pack);
+    const size_t fbytes = (size_t)c->n_cells * c->grid.q * elem_size(c->grid.storage);
+    lbm_status s = pack(c, 0, pk);
+    if (s != LBM_OK) return s;
+    LBM_CUDA(cudaMemcpyAsync(pk + fbytes, c->base.omega, (size_t)c->n_cells * 4, cudaMemcpyDeviceToDevice, c->stream),
+             "save omega");
+    const cudaMemcpyKind k = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    char* d = static_cast<char*>(dst);
+    LBM_CUDA(cudaMemcpyAsync(d + kHeader, pk, need - kHeader, k, c->stream), "save copy");
+    if (dst_on_device)
+        LBM_CUDA(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream), "save header");
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "save sync");
+    if (!dst_on_device) std::memcpy(d, &h, sizeof(h));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_load(lbm_ctx* c, const void* src, size_t bytes, int32_t src_on_device)
+{
+    if (!c || !src) return LBM_EINVAL;
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    const size_t need = lbm_state_size(c);
+    if (bytes < need) return fail(c, LBM_EINVAL, "source smaller than lbm_state_size");
+    StateHeader h{};
+    const char* s = static_cast<const char*>(src);
+    if (src_on_device) {
+        LBM_CUDA(cudaMemcpyAsync(&h, s, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "load header");
+        LBM_CUDA(cudaStreamSynchronize(c->stream), "load sync");
+    } else {
+        std::memcpy(&h, s, sizeof(h));
+    }
+    if (h.magic != kStateMagic || h.n_cells != c->n_cells || h.q != c->grid.q || h.storage != c->grid.storage)
+        return fail(c, LBM_EINVAL, "checkpoint does not match this context");
+    char* pk = c->at<char>(c->L.pack);
+    const size_t fbytes = (size_t)c->n_cells * c->grid.q * elem_size(c->grid.storage);
+    LBM_CUDA(cudaMemcpyAsync(pk, s + kHeader, need - kHeader,
+                             src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+             "load copy");
+    lbm_status st = pack(c, 1, pk);
+    if (st != LBM_OK) return st;
+    LBM_CUDA(cudaMemcpyAsync(c->base.omega, pk + fbytes, (size_t)c->n_cells * 4, cudaMemcpyDeviceToDevice, c->stream),
+             "load omega");
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "load sync");
+    c->t = h.t;
+    return LBM_OK;
+}
+
+extern "C" int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
+extern "C" int64_t lbm_fluid_count(const lbm_ctx* c) { return c ? c->n_cells : -1; }
+extern "C" const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+extern "C" void lbm_destroy(lbm_ctx* c) { delete c; }

@@ -1,0 +1,47 @@
+// Declarations of the set-up and utility kernels (setup.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int kSetupThreads = 256;
+constexpr int kSetupCellsPerThread = 16;
+constexpr int kSetupChunk = kSetupThreads * kSetupCellsPerThread;
+
+// Error bits raised by setup_mask.
+constexpr uint32_t kErrPorosity = 1u;  // porosity outside (0, 1] on a non-solid cell
+constexpr uint32_t kErrInlet = 2u;     // inlet cell off its face, no inlet, or phi != 1
+constexpr uint32_t kErrOutlet = 4u;    // outlet cell off its face, or without a fluid phi = 1 neighbour
+
+struct SetupParams {
+    int nx, ny, nz;
+    int periodic[3];
+    int n_cells, n_bulk;
+    const uint8_t* flags;
+    const float* phi;
+    const uint32_t* cells;
+    uint32_t* mask;
+    float* bnd_prof;
+    uint32_t* bnd_nbmask;
+    int in_axis, in_side, out_axis, out_side;
+    double in_center[3];
+    double in_radius;
+    uint32_t* err;
+};
+
+// Host launchers (setup.cu).  phase 0 of launch_setup_cells counts and scans,
+// phase 1 emits the list.
+cudaError_t launch_setup_cells(const uint8_t* flags, long long N, int nx, int ny, uint32_t* counts,
+                               uint32_t* offsets, uint32_t* totals, cudaStream_t s, int phase, uint32_t* cells);
+cudaError_t launch_setup_mask(int q, const SetupParams& S, cudaStream_t s);
+cudaError_t launch_init_state(int storage, const uint32_t* cells, int n_cells, int nx, int ny, long long N, int Q,
+                              void* f, float* omega, float omega0, cudaStream_t s);
+cudaError_t launch_pack_state(int storage, const uint32_t* cells, int n_cells, int nx, int ny, long long N, int Q,
+                              void* f, void* state, int unpack, cudaStream_t s);
+cudaError_t launch_diag_finish(const double* partials, int nblk, double* out, cudaStream_t s);
+
+}  // namespace lbm

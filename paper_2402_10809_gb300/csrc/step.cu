@@ -1,0 +1,44 @@
+// One translation unit per (velocity set, storage type): compiled several
+// times with -DLBM_Q=19|27 and -DLBM_STORE=0|1|2 so the large unrolled
+// kernels build in parallel.  Exports a host launcher per instantiation.
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+#ifndef LBM_Q
+#error "LBM_Q must be defined"
+#endif
+#ifndef LBM_STORE
+#error "LBM_STORE must be defined"
+#endif
+
+#if LBM_STORE == 0
+#define LBM_T float
+#define LBM_TNAME f32
+#elif LBM_STORE == 1
+#define LBM_T __half
+#define LBM_TNAME f16
+#else
+#define LBM_T __nv_bfloat16
+#define LBM_TNAME bf16
+#endif
+
+#define LBM_CAT2(a, b, c) launch_step_##a##_##b
+#define LBM_CAT(a, b) LBM_CAT2(a, b, 0)
+#define LBM_LAUNCHER LBM_CAT(LBM_Q, LBM_TNAME)
+
+namespace lbm {
+
+cudaError_t LBM_LAUNCHER(int mode, const Params& P, cudaStream_t s)
+{
+    const int grid = (P.n_cells + kBlock - 1) / kBlock;
+    if (grid == 0) return cudaSuccess;
+    switch (mode) {
+        case kModeStep: lbm_kernel<LBM_Q, LBM_T, kModeStep><<<grid, kBlock, 0, s>>>(P); break;
+        case kModeMoments: lbm_kernel<LBM_Q, LBM_T, kModeMoments><<<grid, kBlock, 0, s>>>(P); break;
+        default: lbm_kernel<LBM_Q, LBM_T, kModeDiag><<<grid, kBlock, 0, s>>>(P); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,297 @@
+"""Python binding of the C ABI in include/lbm.h (ctypes; argument marshalling only).
+
+Every compute step runs in the CUDA kernels of liblbm.so.  PyTorch provides the
+device workspace and the stream.  The binding fails loudly when the library is
+missing or cannot be loaded; there is no CPU fallback.
+"""
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE = range(6)
+LBM_SOLID, LBM_FLUID, LBM_INLET, LBM_OUTLET = range(4)
+LBM_F32, LBM_F16DEV, LBM_BF16DEV = range(3)
+STORAGE = {"f32": LBM_F32, "f16dev": LBM_F16DEV, "bf16dev": LBM_BF16DEV}
+STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EUNSTABLE", 5: "LBM_ESTATE"}
+
+# Symbols include/lbm.h declares (checked by the tests).
+SYMBOLS = ["lbm_workspace_size", "lbm_init", "lbm_step", "lbm_moments", "lbm_diag", "lbm_set_check",
+           "lbm_state_size", "lbm_save", "lbm_load", "lbm_time", "lbm_fluid_count", "lbm_last_error",
+           "lbm_destroy"]
+
+
+class lbm_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("q", C.c_int32),
+                ("storage", C.c_int32), ("periodic", C.c_int32 * 3)]
+
+
+class lbm_rheology(C.Structure):
+    _fields_ = [("mu0", C.c_double), ("mu_inf", C.c_double), ("lambda_", C.c_double), ("n", C.c_double),
+                ("a", C.c_double), ("rho0", C.c_double), ("dx", C.c_double), ("dt", C.c_double)]
+
+
+class lbm_porous(C.Structure):
+    _fields_ = [("d_p", C.c_double), ("k_const", C.c_double), ("nu_darcy", C.c_double),
+                ("forchheimer", C.c_int32)]
+
+
+class lbm_bc(C.Structure):
+    _fields_ = [("body_force", C.c_double * 3), ("inlet_axis", C.c_int32), ("inlet_side", C.c_int32),
+                ("inlet_center", C.c_double * 3), ("inlet_radius", C.c_double), ("u0", C.c_double),
+                ("amp", C.c_double), ("period", C.c_double), ("ramp_steps", C.c_double),
+                ("outlet_axis", C.c_int32), ("outlet_side", C.c_int32), ("rho_out", C.c_double)]
+
+
+_lib = None
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Loads liblbm.so (building it in-tree first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build()")
+    L = C.CDLL(path)
+    P, vp = C.POINTER, C.c_void_p
+    L.lbm_workspace_size.restype = C.c_size_t
+    L.lbm_workspace_size.argtypes = [P(lbm_grid), C.c_int64]
+    L.lbm_init.restype = C.c_int
+    L.lbm_init.argtypes = [P(vp), P(lbm_grid), vp, vp, C.c_int32, P(lbm_rheology), P(lbm_porous), P(lbm_bc),
+                           vp, C.c_size_t, vp]
+    L.lbm_step.restype = C.c_int
+    L.lbm_step.argtypes = [vp, C.c_int32]
+    L.lbm_moments.restype = C.c_int
+    L.lbm_moments.argtypes = [vp, vp, vp, vp, vp, C.c_int32]
+    L.lbm_diag.restype = C.c_int
+    L.lbm_diag.argtypes = [vp, vp, C.c_int32, P(C.c_double)]
+    L.lbm_set_check.restype = C.c_int
+    L.lbm_set_check.argtypes = [vp, C.c_int32]
+    L.lbm_state_size.restype = C.c_size_t
+    L.lbm_state_size.argtypes = [vp]
+    L.lbm_save.restype = C.c_int
+    L.lbm_save.argtypes = [vp, vp, C.c_size_t, C.c_int32]
+    L.lbm_load.restype = C.c_int
+    L.lbm_load.argtypes = [vp, vp, C.c_size_t, C.c_int32]
+    L.lbm_time.restype = C.c_int64
+    L.lbm_time.argtypes = [vp]
+    L.lbm_fluid_count.restype = C.c_int64
+    L.lbm_fluid_count.argtypes = [vp]
+    L.lbm_last_error.restype = C.c_char_p
+    L.lbm_last_error.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    L.lbm_destroy.argtypes = [vp]
+    _lib = L
+    return L
+
+
+def _check(ctx, status):
+    if status != LBM_OK:
+        msg = load().lbm_last_error(ctx).decode() if ctx else ""
+        raise LBMError(status, msg)
+
+
+# ----------------------------------------------------------------- structs
+
+def make_grid(dims, q, storage, periodic):
+    g = lbm_grid()
+    g.nx, g.ny, g.nz = dims
+    g.q = q
+    g.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    g.periodic = (C.c_int32 * 3)(*[int(p) for p in periodic])
+    return g
+
+
+def make_params(rheology, porous, bc):
+    r = lbm_rheology(rheology["mu0"], rheology["mu_inf"], rheology["lam"], rheology["n"], rheology["a"],
+                     rheology["rho0"], rheology["dx"], rheology["dt"])
+    p = lbm_porous(porous["d_p"], porous["k_const"], porous["nu_darcy"], int(porous["forchheimer"]))
+    b = lbm_bc()
+    b.body_force = (C.c_double * 3)(*bc["body_force"])
+    b.inlet_axis, b.inlet_side = bc["inlet_axis"], bc["inlet_side"]
+    b.inlet_center = (C.c_double * 3)(*bc["inlet_center"])
+    b.inlet_radius, b.u0, b.amp = bc["inlet_radius"], bc["u0"], bc["amp"]
+    b.period, b.ramp_steps = bc["period"], bc["ramp_steps"]
+    b.outlet_axis, b.outlet_side, b.rho_out = bc["outlet_axis"], bc["outlet_side"], bc["rho_out"]
+    return r, p, b
+
+
+# ----------------------------------------------------------------- C ABI, same names
+
+def lbm_workspace_size(grid, n_fluid=-1):
+    return int(load().lbm_workspace_size(C.byref(grid), int(n_fluid)))
+
+
+def lbm_init(grid, flags, porosity, inputs_on_device, rheology, porous, bc, workspace, workspace_bytes, stream):
+    """Returns a context handle.  flags / porosity / workspace are raw addresses
+    (ints) of host or device memory; stream is a cudaStream_t as int."""
+    h = C.c_void_p()
+    st = load().lbm_init(C.byref(h), C.byref(grid), C.c_void_p(flags), C.c_void_p(porosity),
+                         int(inputs_on_device), C.byref(rheology), C.byref(porous), C.byref(bc),
+                         C.c_void_p(workspace), C.c_size_t(workspace_bytes), C.c_void_p(stream))
+    if st != LBM_OK:
+        msg = load().lbm_last_error(h).decode() if h else ""
+        if h:
+            load().lbm_destroy(h)
+        raise LBMError(st, msg)
+    return h
+
+
+def lbm_step(ctx, n):
+    _check(ctx, load().lbm_step(ctx, int(n)))
+
+
+def lbm_moments(ctx, rho, u, shear_rate, omega, dst_on_device):
+    _check(ctx, load().lbm_moments(ctx, C.c_void_p(rho), C.c_void_p(u), C.c_void_p(shear_rate),
+                                   C.c_void_p(omega), int(dst_on_device)))
+
+
+def lbm_diag(ctx, region, region_on_device):
+    out = (C.c_double * 8)()
+    _check(ctx, load().lbm_diag(ctx, C.c_void_p(region), int(region_on_device), out))
+    return np.array(out[:], dtype=np.float64)
+
+
+def lbm_set_check(ctx, check_every):
+    _check(ctx, load().lbm_set_check(ctx, int(check_every)))
+
+
+def lbm_state_size(ctx):
+    return int(load().lbm_state_size(ctx))
+
+
+def lbm_save(ctx, dst, nbytes, dst_on_device):
+    _check(ctx, load().lbm_save(ctx, C.c_void_p(dst), C.c_size_t(nbytes), int(dst_on_device)))
+
+
+def lbm_load(ctx, src, nbytes, src_on_device):
+    _check(ctx, load().lbm_load(ctx, C.c_void_p(src), C.c_size_t(nbytes), int(src_on_device)))
+
+
+def lbm_time(ctx):
+    return int(load().lbm_time(ctx))
+
+
+def lbm_fluid_count(ctx):
+    return int(load().lbm_fluid_count(ctx))
+
+
+def lbm_last_error(ctx):
+    return load().lbm_last_error(ctx).decode()
+
+
+def lbm_destroy(ctx):
+    load().lbm_destroy(ctx)
+
+
+# ----------------------------------------------------------------- convenience owner
+
+class Simulation:
+    """Owns one context plus its torch workspace on a CUDA device.
+
+    ``problem`` is a lbm_inputs.Problem (or anything with dims, q, periodic,
+    flags, phi, rheology, porous, bc).  Inputs are passed from host memory
+    unless ``inputs_on_device`` is set, in which case they are copied to the
+    device first through torch.
+    """
+
+    def __init__(self, problem, storage="f32", device="cuda", stream=None, inputs_on_device=False):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.problem = problem
+        self.grid = make_grid(problem.dims, problem.q, storage, problem.periodic)
+        self.rheo, self.por, self.bc = make_params(problem.rheology, problem.porous, problem.bc)
+        flags = np.ascontiguousarray(problem.flags, dtype=np.uint8)
+        phi = np.ascontiguousarray(problem.phi, dtype=np.float32)
+        n_fluid = int(np.count_nonzero(flags))
+        nbytes = lbm_workspace_size(self.grid, n_fluid)
+        if nbytes == 0:
+            raise LBMError(LBM_EINVAL, "bad grid")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if inputs_on_device:
+            dflags = torch.from_numpy(flags).to(self.device)
+            dphi = torch.from_numpy(phi).to(self.device)
+            fp, pp = dflags.data_ptr(), dphi.data_ptr()
+        else:
+            fp, pp = flags.ctypes.data, phi.ctypes.data
+        with torch.cuda.device(self.device):
+            self.ctx = lbm_init(self.grid, fp, pp, int(inputs_on_device), self.rheo, self.por, self.bc,
+                                self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        if inputs_on_device:
+            self.stream.synchronize()
+        self.N = int(flags.size)
+        self.shape = flags.shape
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def t(self):
+        return lbm_time(self.ctx)
+
+    @property
+    def n_fluid(self):
+        return lbm_fluid_count(self.ctx)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def moments(self, on_device=False):
+        """rho, u (3, ...), gdot, omega of the current time on the dense box."""
+        torch = self.torch
+        if on_device:
+            out = torch.empty((6,) + self.shape, dtype=torch.float32, device=self.device)
+            lbm_moments(self.ctx, out[0].data_ptr(), out[1].data_ptr(), out[4].data_ptr(), out[5].data_ptr(), 1)
+            return dict(rho=out[0], u=out[1:4], gdot=out[4], omega=out[5])
+        rho = np.zeros(self.shape, np.float32)
+        u = np.zeros((3,) + self.shape, np.float32)
+        g = np.zeros(self.shape, np.float32)
+        om = np.zeros(self.shape, np.float32)
+        lbm_moments(self.ctx, rho.ctypes.data, u.ctypes.data, g.ctypes.data, om.ctypes.data, 0)
+        return dict(rho=rho, u=u, gdot=g, omega=om)
+
+    def diag(self, region=None):
+        if region is None:
+            return lbm_diag(self.ctx, None, 0)
+        if hasattr(region, "data_ptr"):
+            return lbm_diag(self.ctx, region.data_ptr(), 1)
+        reg = np.ascontiguousarray(region, dtype=np.uint8)
+        return lbm_diag(self.ctx, reg.ctypes.data, 0)
+
+    def save(self):
+        n = lbm_state_size(self.ctx)
+        buf = np.zeros(n, np.uint8)
+        lbm_save(self.ctx, buf.ctypes.data, n, 0)
+        return buf
+
+    def load_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        lbm_load(self.ctx, buf.ctypes.data, buf.size, 0)

@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads and exports every function include/lbm.h
+declares; host-only argument handling (no CUDA work) behaves as documented."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2402_10809_gb300 import lbm
+
+    L = lbm.load()
+    declared = _declared()
+    assert declared, "no declarations found"
+    assert declared == set(lbm.SYMBOLS)
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def test_workspace_size_host_logic():
+    from paper_2402_10809_gb300 import lbm
+
+    g = lbm.make_grid((32, 32, 64), 19, "f32", (0, 0, 1))
+    full = lbm.lbm_workspace_size(g, -1)
+    tight = lbm.lbm_workspace_size(g, 39424)
+    assert full > tight > 2 * 19 * 32 * 32 * 64 * 4
+    g16 = lbm.make_grid((32, 32, 64), 19, "f16dev", (0, 0, 1))
+    assert lbm.lbm_workspace_size(g16, 39424) < tight
+    bad = lbm.make_grid((32, 32, 64), 20, "f32", (0, 0, 1))
+    assert lbm.lbm_workspace_size(bad, 10) == 0
+    huge = lbm.make_grid((2048, 2, 2), 19, "f32", (0, 0, 0))
+    assert lbm.lbm_workspace_size(huge, 10) == 0
+
+
+def test_init_rejects_bad_arguments_before_any_device_work():
+    from paper_2402_10809_gb300 import lbm
+    from lbm_inputs import pipe_problem
+
+    prob = pipe_problem()
+    r, p, b = lbm.make_params(prob.rheology, prob.porous, prob.bc)
+    g = lbm.make_grid(prob.dims, 23, "f32", prob.periodic)  # q must be 19 or 27
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_init(g, 1, 1, 0, r, p, b, 256, 1 << 20, 0)
+    assert e.value.status == lbm.LBM_EINVAL
+    g = lbm.make_grid(prob.dims, 19, "f32", prob.periodic)
+    with pytest.raises(lbm.LBMError) as e:  # misaligned workspace
+        lbm.lbm_init(g, 1, 1, 0, r, p, b, 257, 1 << 20, 0)
+    assert e.value.status == lbm.LBM_EINVAL
+    r.mu0 = -1.0
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_init(g, 1, 1, 0, r, p, b, 256, 1 << 20, 0)
+    assert e.value.status == lbm.LBM_EINVAL
+
+
+def test_null_context_calls_are_safe():
+    from paper_2402_10809_gb300 import lbm
+
+    L = lbm.load()
+    assert L.lbm_step(None, 1) == lbm.LBM_EINVAL
+    assert L.lbm_time(None) == -1
+    assert L.lbm_state_size(None) == 0
+    L.lbm_destroy(None)
