@@ -140,6 +140,24 @@ lbm_status lbm_moments(lbm_ctx* ctx, float* rho, float* u, float* shear_rate, fl
  * tells where it lives.  out is host memory; the call synchronises. */
 lbm_status lbm_diag(lbm_ctx* ctx, const uint8_t* region, int32_t region_on_device, double out[8]);
 
+/* lbm_diag without caller scratch (the paper has no counterpart; this is a
+ * deployment convenience).  Same outputs as lbm_diag, computed by the same
+ * kernels, but the per-block partial sums and the device-side result live in a
+ * fixed array inside the library instead of the caller's workspace, and the
+ * call allocates nothing.  It is meant for callers that may not allocate
+ * device memory where they need the diagnostics, e.g. a monitoring thread of a
+ * host application whose device allocator is owned by another framework.
+ *  - Limit: at most 8,388,608 non-solid cells (LBM_EINVAL beyond, use lbm_diag);
+ *    the array costs every GPU that loads the library 2.25 MiB until exit.
+ *  - region: device memory or NULL (host regions are rejected with LBM_EINVAL,
+ *    since copying them would need scratch); out: host memory; synchronises.
+ *  - The context's device must be current.  The first call on a device looks
+ *    up the array's device address (cudaGetSymbolAddress); make that first
+ *    call before any stream capture begins.
+ *  - All calls share the array: calls that overlap on the GPU race; serialise
+ *    them.  No state carries over from one call to the next. */
+lbm_status lbm_diag_noalloc(lbm_ctx* ctx, const uint8_t* region, double out[8]);
+
 /* Every check_every steps of later lbm_step calls, run the non-finite count of
  * lbm_diag and return LBM_EUNSTABLE when it is nonzero (0 = never, default). */
 lbm_status lbm_set_check(lbm_ctx* ctx, int32_t check_every);

@@ -518,3 +518,97 @@ extern "C" int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 extern "C" int64_t lbm_fluid_count(const lbm_ctx* c) { return c ? c->n_cells : -1; }
 extern "C" const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
 extern "C" void lbm_destroy(lbm_ctx* c) { delete c; }
+
+// ---------------------------------------------------------------------------
+// Diagnostics without any caller-provided scratch.
+//
+// lbm_diag reduces into per-block partial sums kept in the caller's workspace.
+// lbm_diag_noalloc computes the same numbers with the same kernels, but keeps
+// those partial sums and the device-side result in the fixed array below, so it
+// needs no scratch from the caller and never allocates.  It serves callers that
+// may not allocate device memory at the point of the call: a monitoring thread
+// attached to a running simulation whose allocator belongs to another framework,
+// or code running where allocation is forbidden or unsafe.
+//
+// The array is a file-scope __device__ variable: every GPU that loads the
+// library holds kNoAllocBytes for it until the process exits.  Its device
+// address is looked up once per device with cudaGetSymbolAddress (the name in
+// host code is only a host-side stand-in and must never be handed to a kernel).
+// The first lbm_diag_noalloc call on a device performs that lookup, so make
+// that first call before any stream capture begins.  All calls share the one
+// array: calls that overlap on the GPU (other streams, other threads) race and
+// must be serialised by the caller.  Every slot a call reads is written earlier
+// in the same call, so leftover contents of a previous call do no harm.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr long long kNoAllocMaxCells = 8LL * 1024 * 1024;  // non-solid cells
+constexpr long long kNoAllocMaxBlocks = kNoAllocMaxCells / kBlock;
+constexpr size_t kNoAllocSlots = (size_t)kNoAllocMaxBlocks * kDiagSlots + 8;  // partials + result
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocSlots];
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (set-up, once per device).
+cudaError_t noalloc_scratch(int dev, double** out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_diag_noalloc(lbm_ctx* c, const uint8_t* region, double out[8])
+{
+    if (!c || !out) return LBM_EINVAL;
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    if (c->n_cells > kNoAllocMaxCells)
+        return fail(c, LBM_EINVAL, "lbm_diag_noalloc handles at most " + std::to_string(kNoAllocMaxCells) +
+                                       " non-solid cells, this context has " + std::to_string(c->n_cells) +
+                                       "; use lbm_diag");
+    cudaPointerAttributes attr{};
+    LBM_CUDA(cudaPointerGetAttributes(&attr, c->ws), "workspace attributes");
+    int dev = -1;
+    LBM_CUDA(cudaGetDevice(&dev), "current device");
+    if (attr.type != cudaMemoryTypeDevice || attr.device != dev)
+        return fail(c, LBM_EINVAL, "make the context's device current before lbm_diag_noalloc");
+    if (dev < 0 || dev >= kMaxDevices) return fail(c, LBM_EINVAL, "device ordinal out of range");
+    if (region) {
+        cudaPointerAttributes ra{};
+        LBM_CUDA(cudaPointerGetAttributes(&ra, region), "region attributes");
+        if (ra.type != cudaMemoryTypeDevice && ra.type != cudaMemoryTypeManaged)
+            return fail(c, LBM_EINVAL, "lbm_diag_noalloc needs the region in device memory (or NULL)");
+    }
+    if (c->n_cells == 0) {
+        for (int k = 0; k < 8; ++k) out[k] = 0.0;
+        return LBM_OK;
+    }
+    double* scratch = nullptr;
+    LBM_CUDA(noalloc_scratch(dev, &scratch), "cudaGetSymbolAddress of the diagnostics scratch");
+    double* partials = scratch;
+    double* result = scratch + (size_t)kNoAllocMaxBlocks * kDiagSlots;
+    Params P = c->base;
+    P.fsrc = c->f(c->cur);
+    P.fdst = nullptr;
+    P.t = c->t;
+    P.region = region;
+    P.partials = partials;
+    LBM_CUDA(launch(c->grid, kModeDiag, P, c->stream), "diag kernel");
+    const int nblk = (c->n_cells + kBlock - 1) / kBlock;
+    LBM_CUDA(launch_diag_finish(partials, nblk, result, c->stream), "diag reduction");
+    LBM_CUDA(cudaMemcpyAsync(out, result, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "diag copy");
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "diag sync");
+    return LBM_OK;
+}

@@ -19,7 +19,8 @@ STORAGE = {"f32": LBM_F32, "f16dev": LBM_F16DEV, "bf16dev": LBM_BF16DEV}
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EUNSTABLE", 5: "LBM_ESTATE"}
 
 # Symbols include/lbm.h declares (checked by the tests).
-SYMBOLS = ["lbm_workspace_size", "lbm_init", "lbm_step", "lbm_moments", "lbm_diag", "lbm_set_check",
+SYMBOLS = ["lbm_workspace_size", "lbm_init", "lbm_step", "lbm_moments", "lbm_diag", "lbm_diag_noalloc",
+           "lbm_set_check",
            "lbm_state_size", "lbm_save", "lbm_load", "lbm_time", "lbm_fluid_count", "lbm_last_error",
            "lbm_destroy"]
 
@@ -82,6 +83,8 @@ def load(build_if_missing=True):
     L.lbm_moments.argtypes = [vp, vp, vp, vp, vp, C.c_int32]
     L.lbm_diag.restype = C.c_int
     L.lbm_diag.argtypes = [vp, vp, C.c_int32, P(C.c_double)]
+    L.lbm_diag_noalloc.restype = C.c_int
+    L.lbm_diag_noalloc.argtypes = [vp, vp, P(C.c_double)]
     L.lbm_set_check.restype = C.c_int
     L.lbm_set_check.argtypes = [vp, C.c_int32]
     L.lbm_state_size.restype = C.c_size_t
@@ -166,6 +169,14 @@ def lbm_moments(ctx, rho, u, shear_rate, omega, dst_on_device):
 def lbm_diag(ctx, region, region_on_device):
     out = (C.c_double * 8)()
     _check(ctx, load().lbm_diag(ctx, C.c_void_p(region), int(region_on_device), out))
+    return np.array(out[:], dtype=np.float64)
+
+
+def lbm_diag_noalloc(ctx, region_device):
+    """lbm_diag for callers without scratch memory; region_device is a device
+    address or None."""
+    out = (C.c_double * 8)()
+    _check(ctx, load().lbm_diag_noalloc(ctx, C.c_void_p(region_device), out))
     return np.array(out[:], dtype=np.float64)
 
 
