@@ -8,18 +8,20 @@ from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
+CSRC = os.environ.get("LBM_CSRC") or os.path.join(HERE, "csrc")
+# LBM_BUILD_DIR / LBM_NVCC_EXTRA redirect the build and add nvcc flags (tuning runs)
+BUILD = os.environ.get("LBM_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "-I", CSRC, "-I", os.path.join(ROOT, "include")]
 
+EXTRA = os.environ.get("LBM_NVCC_EXTRA", "").split()
 UNITS = [("setup", "setup.cu", []), ("api", "api.cu", [])]
 for q in (19, 27):
     for s, name in ((0, "f32"), (1, "f16"), (2, "bf16")):
-        UNITS.append((f"step_{q}_{name}", "step.cu", [f"-DLBM_Q={q}", f"-DLBM_STORE={s}"]))
+        UNITS.append((f"step_{q}_{name}", "step.cu", [f"-DLBM_Q={q}", f"-DLBM_STORE={s}", "--use_fast_math"]))
 
 
 def _sources():
@@ -30,13 +32,16 @@ def up_to_date():
     if not os.path.exists(LIB):
         return False
     t = os.path.getmtime(LIB)
+    stamp = os.path.join(BUILD, "flags.txt")
+    if not os.path.exists(stamp) or open(stamp).read() != " ".join(EXTRA):
+        return False
     return all(os.path.getmtime(s) <= t for s in _sources())
 
 
 def _compile(unit):
     name, src, defs = unit
     obj = os.path.join(BUILD, name + ".o")
-    cmd = [NVCC, *ARCH, *FLAGS, *defs, "-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [NVCC, *ARCH, *FLAGS, *defs, *EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     with open(os.path.join(BUILD, name + ".log"), "w") as fh:
         fh.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
@@ -60,6 +65,8 @@ def build(force=False, jobs=None):
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
     os.replace(tmp, LIB)
+    with open(os.path.join(BUILD, "flags.txt"), "w") as fh:
+        fh.write(" ".join(EXTRA))
     return LIB
 
 

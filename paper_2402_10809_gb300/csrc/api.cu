@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -64,8 +65,8 @@ Layout layout(const lbm_grid* g, long long nf)
     L.phi = take((size_t)N * 4);
     L.flags = take((size_t)N);
     L.region = take((size_t)N);
-    L.counts = take((size_t)nblk * 3 * 4);
-    L.offsets = take((size_t)nblk * 3 * 4);
+    L.counts = take((size_t)nblk * kCategories * 4);
+    L.offsets = take((size_t)nblk * kCategories * 4);
     L.totals = take(16);
     L.err = take(32);
     L.diag_out = take(8 * 8);
@@ -76,7 +77,7 @@ Layout layout(const lbm_grid* g, long long nf)
     L.omega = take(n * 4);
     L.bnd_prof = take(n * 4);
     L.bnd_nbmask = take(n * 4);
-    L.partials = take(((n + kBlock - 1) / kBlock) * kDiagSlots * 8);
+    L.partials = take(((n + kBlock - 1) / kBlock + 1) * kDiagSlots * 8);  // fast + general block ranges
     L.staging = take(n * 6 * 4);
     L.pack = take(n * ((size_t)g->q * elem_size(g->storage) + 4));
     L.end = o;
@@ -107,7 +108,7 @@ struct lbm_ctx {
     size_t ws_bytes = 0;
     Layout L{};
     long long N = 0;
-    int n_cells = 0, n_bulk = 0, n_in = 0, n_out = 0;
+    int n_cells = 0, n_fast = 0, n_bulk = 0, n_in = 0, n_out = 0;
     int cur = 0;
     long long t = 0;
     int check_every = 0;
@@ -156,7 +157,7 @@ static lbm_status run_diag(lbm_ctx* c, const uint8_t* region_dev, double out[8])
     P.region = region_dev;
     P.partials = c->at<double>(c->L.partials);
     LBM_CUDA(launch(c->grid, kModeDiag, P, c->stream), "diag kernel");
-    const int nblk = (c->n_cells + kBlock - 1) / kBlock;
+    const int nblk = total_blocks(P);
     double* dout = c->at<double>(c->L.diag_out);
     if (nblk > 0) {
         LBM_CUDA(launch_diag_finish(P.partials, nblk, dout, c->stream), "diag reduction");
@@ -206,21 +207,24 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     LBM_CUDA(cudaMemcpyAsync(c->at<float>(c->L.phi), porosity, (size_t)c->N * 4, kind, c->stream), "copy porosity");
 
     // cell list: count, scan, emit
-    LBM_CUDA(launch_setup_cells(c->at<uint8_t>(c->L.flags), c->N, grid->nx, grid->ny, c->at<uint32_t>(c->L.counts),
+    CellGrid CG{grid->nx, grid->ny, grid->nz, {grid->periodic[0] ? 1 : 0, grid->periodic[1] ? 1 : 0,
+                                                grid->periodic[2] ? 1 : 0}};
+    LBM_CUDA(launch_setup_cells(c->at<uint8_t>(c->L.flags), c->N, CG, c->at<uint32_t>(c->L.counts),
                                 c->at<uint32_t>(c->L.offsets), c->at<uint32_t>(c->L.totals), c->stream, 0, nullptr),
              "setup count");
-    uint32_t tot[3] = {0, 0, 0};
+    uint32_t tot[kCategories] = {0, 0, 0, 0};
     LBM_CUDA(cudaMemcpyAsync(tot, c->at<uint32_t>(c->L.totals), sizeof(tot), cudaMemcpyDeviceToHost, c->stream),
              "copy totals");
     LBM_CUDA(cudaStreamSynchronize(c->stream), "setup sync");
-    c->n_bulk = (int)tot[0];
-    c->n_in = (int)tot[1];
-    c->n_out = (int)tot[2];
+    c->n_fast = (int)tot[0];
+    c->n_bulk = (int)(tot[0] + tot[1]);
+    c->n_in = (int)tot[2];
+    c->n_out = (int)tot[3];
     c->n_cells = c->n_bulk + c->n_in + c->n_out;
     c->L = layout(grid, c->n_cells);
     if (workspace_bytes < c->L.end)
         return fail(c, LBM_ENOMEM, "workspace smaller than lbm_workspace_size(grid, " + std::to_string(c->n_cells) + ")");
-    LBM_CUDA(launch_setup_cells(c->at<uint8_t>(c->L.flags), c->N, grid->nx, grid->ny, c->at<uint32_t>(c->L.counts),
+    LBM_CUDA(launch_setup_cells(c->at<uint8_t>(c->L.flags), c->N, CG, c->at<uint32_t>(c->L.counts),
                                 c->at<uint32_t>(c->L.offsets), c->at<uint32_t>(c->L.totals), c->stream, 1,
                                 c->at<uint32_t>(c->L.cells)),
              "setup emit");
@@ -286,6 +290,9 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     P.nz = grid->nz;
     P.N = c->N;
     P.n_cells = c->n_cells;
+    // the fast path indexes the distribution buffers with 32-bit element
+    // offsets; boxes beyond that run every cell through the general path
+    P.n_fast = (unsigned long long)grid->q * (unsigned long long)c->N < (1ull << 32) ? c->n_fast : 0;
     P.n_bulk = c->n_bulk;
     P.cells = S.cells;
     P.mask = S.mask;
@@ -398,15 +405,10 @@ extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho, float* u, float* shear
     }
     LBM_CUDA(cudaStreamSynchronize(c->stream), "moments sync");
     float* outs[6] = {rho, u, u ? u + N : nullptr, u ? u + 2 * N : nullptr, shear_rate, omega};
-    const long long plane = (long long)c->grid.nx * c->grid.ny;
     for (int k = 0; k < 6; ++k) {
         if (!outs[k]) continue;
         std::memset(outs[k], 0, N * 4);
-        for (size_t p = 0; p < n; ++p) {
-            const uint32_t pc = c->host_cells[p];
-            const long long idx = (pc & 1023u) + (long long)c->grid.nx * ((pc >> 10) & 1023u) + plane * (pc >> 20);
-            outs[k][idx] = h[k * n + p];
-        }
+        for (size_t p = 0; p < n; ++p) outs[k][c->host_cells[p]] = h[k * n + p];
     }
     return LBM_OK;
 }
@@ -546,7 +548,8 @@ namespace {
 
 constexpr long long kNoAllocMaxCells = 8LL * 1024 * 1024;  // non-solid cells
 constexpr long long kNoAllocMaxBlocks = kNoAllocMaxCells / kBlock;
-constexpr size_t kNoAllocSlots = (size_t)kNoAllocMaxBlocks * kDiagSlots + 8;  // partials + result
+// the step kernel's block split (fast + general ranges) may use one block more
+constexpr size_t kNoAllocSlots = (size_t)(kNoAllocMaxBlocks + 1) * kDiagSlots + 8;  // partials + result
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocSlots];
@@ -598,7 +601,7 @@ extern "C" lbm_status lbm_diag_noalloc(lbm_ctx* c, const uint8_t* region, double
     double* scratch = nullptr;
     LBM_CUDA(noalloc_scratch(dev, &scratch), "cudaGetSymbolAddress of the diagnostics scratch");
     double* partials = scratch;
-    double* result = scratch + (size_t)kNoAllocMaxBlocks * kDiagSlots;
+    double* result = scratch + (size_t)(kNoAllocMaxBlocks + 1) * kDiagSlots;
     Params P = c->base;
     P.fsrc = c->f(c->cur);
     P.fdst = nullptr;
@@ -606,7 +609,7 @@ extern "C" lbm_status lbm_diag_noalloc(lbm_ctx* c, const uint8_t* region, double
     P.region = region;
     P.partials = partials;
     LBM_CUDA(launch(c->grid, kModeDiag, P, c->stream), "diag kernel");
-    const int nblk = (c->n_cells + kBlock - 1) / kBlock;
+    const int nblk = total_blocks(P);
     LBM_CUDA(launch_diag_finish(partials, nblk, result, c->stream), "diag reduction");
     LBM_CUDA(cudaMemcpyAsync(out, result, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "diag copy");
     LBM_CUDA(cudaStreamSynchronize(c->stream), "diag sync");

@@ -2,11 +2,14 @@
 // method with Carreau-Yasuda rheology (Horvat et al., arXiv 2402.10809,
 // Sec. 2-4), plus the moments and diagnostics epilogues that reuse its pull.
 //
-// One thread owns one non-solid cell, taken from a compact cell list (bulk
-// cells sorted by dense index, then inlet cells, then outlet cells), so no
-// thread idles on solid voxels of the sparse aneurysm box.  The distributions
-// live in two dense SoA buffers f[i][N]; a warp of consecutive list entries
-// reads and writes consecutive addresses of each direction plane.
+// One thread owns one non-solid cell taken from a compact cell list, so no
+// thread idles on the solid voxels of a sparse aneurysm box.  The list is
+// ordered [plain bulk cells][bulk cells on a periodic face][inlet][outlet];
+// blocks covering the first part run the lean path (kernel-uniform neighbour
+// offsets, no boundary code), blocks covering the rest run the general path.
+// The distributions live in two dense SoA buffers f[i][N]; a warp of
+// consecutive list entries reads and writes consecutive addresses of each
+// direction plane.
 //
 // Stored values are deviations g_i = f_i - w_i phi_hat_i, where phi_hat_i is
 // the porosity of the cell the value streams to (own porosity across solid or
@@ -25,20 +28,26 @@ namespace lbm {
 
 // Per-cell mask word: bit i (i < Q) set when direction i cannot be pulled from
 // its source y - c_i (solid, box wall, or an open face); bits 27-28 cell type;
-// bit 29 set when some fluid neighbour has a different porosity.
+// bit 29 set when some fluid neighbour has a different porosity; bit 30 set
+// when a neighbour lies across a periodic face.
 constexpr uint32_t kTypeShift = 27;
 constexpr uint32_t kPorousBit = 1u << 29;
+constexpr uint32_t kWrapBit = 1u << 30;
 enum { kBulk = 0, kInlet = 1, kOutlet = 2 };
 enum { kModeStep = 0, kModeMoments = 1, kModeDiag = 2 };
 constexpr int kBlock = 256;
 constexpr int kDiagSlots = 9;
+// Resident blocks per SM the step kernel is compiled for (register cap).
+#ifndef LBM_MIN_BLOCKS
+#define LBM_MIN_BLOCKS 3
+#endif
 
 struct Params {
     // geometry
     int nx, ny, nz;
     long long N;
-    int n_cells, n_bulk;
-    const uint32_t* cells;    // packed x | y << 10 | z << 20, list order
+    int n_cells, n_fast, n_bulk;
+    const uint32_t* cells;    // dense index of each listed cell
     const uint32_t* mask;     // list order
     const float* phi;         // dense porosity
     const float* bnd_prof;    // [n_cells - n_bulk]: inlet profile 2 max(0, 1 - r^2/R^2)
@@ -66,6 +75,15 @@ struct Params {
     double* partials;         // [gridDim.x][kDiagSlots]
 };
 
+// Blocks of the launch: the general-path cells [n_fast, n_cells) first, so
+// that their slower blocks overlap the bulk instead of trailing it, then the
+// fast cells [0, n_fast).
+__host__ __device__ inline int general_blocks(const Params& P) { return (P.n_cells - P.n_fast + kBlock - 1) / kBlock; }
+__host__ __device__ inline int total_blocks(const Params& P)
+{
+    return general_blocks(P) + (P.n_fast + kBlock - 1) / kBlock;
+}
+
 // ------------------------------------------------------------------ storage
 
 template <class T>
@@ -89,6 +107,19 @@ struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
 };
 
+// c . v for a lattice vector c with components in {-1, 0, 1}: only the needed
+// additions and sign flips (after unrolling every branch is decided at compile
+// time; IEEE arithmetic would not let the compiler drop 0 * v or v + 0).
+__device__ __forceinline__ float cdot(int cx, int cy, int cz, float x, float y, float z)
+{
+    float r = 0.0f;
+    bool has = false;
+    if (cx != 0) { r = cx > 0 ? x : -x; has = true; }
+    if (cy != 0) { r = has ? (cy > 0 ? r + y : r - y) : (cy > 0 ? y : -y); has = true; }
+    if (cz != 0) { r = has ? (cz > 0 ? r + z : r - z) : (cz > 0 ? z : -z); has = true; }
+    return r;
+}
+
 // ------------------------------------------------------------------ physics
 
 // Darcy and Forchheimer coefficients K1 = phi^2 nu / k, K2 = phi^3 C_F / sqrt(k)
@@ -97,11 +128,11 @@ struct Store<__nv_bfloat16> {
 // and K2 = (1.75 / d)(1 - phi): drag_a = 150 nu / d^2, drag_b = 1.75 / d.  For a
 // constant permeability kc: K1 = (nu / kc) phi^2, K2 = (1.75 / sqrt(150 kc)) phi^1.5,
 // only where phi < 1.
-__device__ __forceinline__ void darcy_coeffs(const Params& P, float phi, float& k1, float& k2)
+__device__ __forceinline__ void darcy_coeffs(const Params& P, float phi, float iphi, float& k1, float& k2)
 {
     if (P.drag_kc) {
         float s = 1.0f - phi;
-        k1 = P.drag_a * s * s / phi;
+        k1 = P.drag_a * s * s * iphi;
         k2 = P.drag_b * s;
     } else if (phi < 1.0f) {
         k1 = P.drag_a * phi * phi;
@@ -131,40 +162,88 @@ __device__ __forceinline__ Macro macroscopic(const Params& P, float phi, float s
     Macro M;
     M.sd = sd;
     M.sigma = phi + sd;
-    float iphi = 1.0f / phi;
+    const float iphi = __frcp_rn(phi);
     M.rho = M.sigma * iphi;
     M.drho = sd * iphi;
-    float isig = 1.0f / M.sigma;
-    float hg = 0.5f * iphi;
-    float vx = mx * isig + P.gx * hg;
-    float vy = my * isig + P.gy * hg;
-    float vz = mz * isig + P.gz * hg;
+    const float isig = __fdividef(1.0f, M.sigma);
+    const float hg = 0.5f * iphi;
+    const float vx = fmaf(P.gx, hg, mx * isig);
+    const float vy = fmaf(P.gy, hg, my * isig);
+    const float vz = fmaf(P.gz, hg, mz * isig);
     float k1, k2;
-    darcy_coeffs(P, phi, k1, k2);
-    float alpha = 0.25f * k1 * iphi;
-    float c1 = 0.5f * k2 * iphi;
-    float c1v = c1 * sqrtf(vx * vx + vy * vy + vz * vz);
-    float c0 = 0.5f + alpha;
-    float r = sqrtf(c0 * c0 + c1v);
-    float dm1 = alpha + (alpha + alpha * alpha + c1v) / (r + 0.5f);
-    float id = 1.0f / (1.0f + dm1);
+    darcy_coeffs(P, phi, iphi, k1, k2);
+    const float alpha = 0.25f * k1 * iphi;
+    const float c1 = 0.5f * k2 * iphi;
+    const float c1v = c1 * sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
+    const float c0 = 0.5f + alpha;
+    const float r = sqrtf(fmaf(c0, c0, c1v));
+    const float dm1 = alpha + __fdividef(fmaf(alpha, alpha, alpha + c1v), r + 0.5f);
+    const float id = __fdividef(1.0f, 1.0f + dm1);
     M.ux = vx * id;
     M.uy = vy * id;
     M.uz = vz * id;
-    float s2 = 2.0f * M.sigma * dm1;
-    M.Fx = M.rho * P.gx - s2 * M.ux;
-    M.Fy = M.rho * P.gy - s2 * M.uy;
-    M.Fz = M.rho * P.gz - s2 * M.uz;
+    const float s2 = 2.0f * M.sigma * dm1;
+    M.Fx = fmaf(M.rho, P.gx, -s2 * M.ux);
+    M.Fy = fmaf(M.rho, P.gy, -s2 * M.uy);
+    M.Fz = fmaf(M.rho, P.gz, -s2 * M.uz);
     return M;
 }
 
 // Carreau-Yasuda law, Eq. (3), and omega = 2 rho c_s^2 / (2 mu + rho c_s^2).
 __device__ __forceinline__ float relaxation_rate(const Params& P, float rho, float gdot)
 {
-    float x = P.lam * gdot;
-    float xa = P.cy_a_two ? x * x : powf(x, P.cy_a);
-    float mu = P.mu_inf + (P.mu0 - P.mu_inf) * exp2f(P.cy_e * log2f(1.0f + xa));
-    return 2.0f * rho / (6.0f * mu + rho);
+    const float x = P.lam * gdot;
+    const float xa = P.cy_a_two ? x * x : __powf(x, P.cy_a);
+    const float mu = fmaf(P.mu0 - P.mu_inf, exp2f(P.cy_e * __log2f(1.0f + xa)), P.mu_inf);
+    return __fdividef(2.0f * rho, fmaf(6.0f, mu, rho));
+}
+
+// ------------------------------------------------------------------ moments
+
+// sum g, sum g c and sum g c c of the Q deviations, factorised by the rows of
+// constant (c_y, c_z) so that every addition is used once.
+template <int Q>
+struct Moments {
+    float sd, mx, my, mz, sxx, syy, szz, sxy, sxz, syz;
+};
+
+// g_i is read from g[i * S] (S = 1: a register array; S = block size: the
+// shared-memory column of one thread).
+template <int Q, int S = 1>
+__device__ __forceinline__ Moments<Q> moments(const float* g)
+{
+    float rs[9], rx[9], rxx[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        const int cy = r % 3 - 1, cz = r / 3 - 1;
+        const int ip = find_dir<Q>(1, cy, cz), im = find_dir<Q>(-1, cy, cz), i0 = find_dir<Q>(0, cy, cz);
+        if (ip >= 0) {
+            rxx[r] = g[ip * S] + g[im * S];
+            rx[r] = g[ip * S] - g[im * S];
+            rs[r] = rxx[r] + g[i0 * S];
+        } else {
+            rxx[r] = 0.0f;
+            rx[r] = 0.0f;
+            rs[r] = g[i0 * S];
+        }
+    }
+    Moments<Q> m;
+    // rows: r = (cy + 1) + 3 (cz + 1)
+    const float ym = rs[0] + rs[3] + rs[6];  // c_y = -1
+    const float yp = rs[2] + rs[5] + rs[8];  // c_y = +1
+    const float zm = rs[0] + rs[1] + rs[2];  // c_z = -1
+    const float zp = rs[6] + rs[7] + rs[8];  // c_z = +1
+    m.sd = (ym + yp) + (rs[1] + rs[4] + rs[7]);
+    m.my = yp - ym;
+    m.syy = yp + ym;
+    m.mz = zp - zm;
+    m.szz = zp + zm;
+    m.mx = ((rx[0] + rx[1]) + (rx[2] + rx[3])) + ((rx[4] + rx[5]) + (rx[6] + rx[7]) + rx[8]);
+    m.sxx = ((rxx[0] + rxx[1]) + (rxx[2] + rxx[3])) + ((rxx[4] + rxx[5]) + (rxx[6] + rxx[7]) + rxx[8]);
+    m.sxy = (rx[2] + rx[5] + rx[8]) - (rx[0] + rx[3] + rx[6]);
+    m.sxz = (rx[6] + rx[7] + rx[8]) - (rx[0] + rx[1] + rx[2]);
+    m.syz = (rs[0] + rs[8]) - (rs[2] + rs[6]);
+    return m;
 }
 
 // ------------------------------------------------------------------ helpers
@@ -195,24 +274,38 @@ __device__ __forceinline__ Coords make_coords(const Params& P, int x, int y, int
     return c;
 }
 
+__device__ __forceinline__ Coords coords_of(const Params& P, uint32_t idx)
+{
+    const uint32_t plane = (uint32_t)P.nx * (uint32_t)P.ny;
+    const uint32_t z = idx / plane;
+    const uint32_t r = idx - z * plane;
+    const uint32_t y = r / (uint32_t)P.nx;
+    return make_coords(P, (int)(r - y * (uint32_t)P.nx), (int)y, (int)z);
+}
+
 // Dense index of y + (dx, dy, dz) with periodic wrap (dx etc. in {-1, 0, 1}).
 __device__ __forceinline__ long long shifted(const Coords& c, int dx, int dy, int dz)
 {
     return c.X[dx + 1] + c.Y[dy + 1] + c.Z[dz + 1];
 }
 
-// Pull of all Q deviations of a cell: g_i = f*_i(y - c_i), or the cell's own
+
+// Source (plane, index) of direction i: g_i = f*_i(y - c_i), or the cell's own
 // f*_opp(i) (half-way bounce-back, Sec. 4) where the source is not available.
-template <int Q, class T>
-__device__ __forceinline__ void pull(const T* __restrict__ f, long long N, const Coords& c, uint32_t mask, float* g)
+template <int Q>
+__device__ __forceinline__ long long pull_offset(long long N, const Coords& c, uint32_t mask, int i)
 {
     using L = Lattice<Q>;
+    return ((mask >> i) & 1u) ? (long long)opp(i) * N + c.idx
+                              : (long long)i * N + shifted(c, -L::cx(i), -L::cy(i), -L::cz(i));
+}
+
+template <int Q, class T>
+__device__ __forceinline__ void pull_general(const T* __restrict__ f, long long N, const Coords& c, uint32_t mask,
+                                             float* g)
+{
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        long long src = ((mask >> i) & 1u) ? (long long)opp(i) * N + c.idx
-                                           : (long long)i * N + shifted(c, -L::cx(i), -L::cy(i), -L::cz(i));
-        g[i] = Store<T>::ld(f + src);
-    }
+    for (int i = 0; i < Q; ++i) g[i] = Store<T>::ld(f + pull_offset<Q>(N, c, mask, i));
 }
 
 // Mean inflow v(t) = u0 (1 + amp sin(2 pi t / period)), linear ramp over the
@@ -235,24 +328,25 @@ __device__ __forceinline__ void zou_he(const Params& P, float prof, float* g)
     using L = Lattice<Q>;
     const int ax = P.in_axis;
     const int sgn = P.in_side == 0 ? 1 : -1;
-    float un = (float)((double)prof * inflow_mean(P, P.t));
-    float ub[3] = {-0.5f * P.gx, -0.5f * P.gy, -0.5f * P.gz};
-    ub[ax] += sgn * un;
-    float ubn = ub[ax] * sgn;
+    const float un = (float)((double)prof * inflow_mean(P, P.t));
+    const float ubx = -0.5f * P.gx + (ax == 0 ? sgn * un : 0.0f);
+    const float uby = -0.5f * P.gy + (ax == 1 ? sgn * un : 0.0f);
+    const float ubz = -0.5f * P.gz + (ax == 2 ? sgn * un : 0.0f);
+    const float ubn = (ax == 0 ? ubx : ax == 1 ? uby : ubz) * sgn;
     float g0 = 0.0f, gm = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        int cn = c_axis<Q>(i, ax) * sgn;
+        const int cn = c_axis<Q>(i, ax) * sgn;
         if (cn == 0) g0 += g[i];
         if (cn < 0) gm += g[i];
     }
-    float drho = (g0 + 2.0f * gm + ubn) / (1.0f - ubn);
-    float rho = 1.0f + drho;
-    float uu = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+    const float drho = (g0 + 2.0f * gm + ubn) / (1.0f - ubn);
+    const float rho = 1.0f + drho;
+    const float uu = ubx * ubx + uby * uby + ubz * ubz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (c_axis<Q>(i, ax) * sgn > 0) {
-            float cu = L::cx(i) * ub[0] + L::cy(i) * ub[1] + L::cz(i) * ub[2];
+            const float cu = cdot(L::cx(i), L::cy(i), L::cz(i), ubx, uby, ubz);
             g[i] = g[opp(i)] + 6.0f * L::w(i) * rho * cu;
         }
     }
@@ -262,16 +356,16 @@ __device__ __forceinline__ void zou_he(const Params& P, float prof, float* g)
         float nres = 0.0f, ncnt = 0.0f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            int cn = c_axis<Q>(i, ax) * sgn;
-            int ct = c_axis<Q>(i, tg);
+            const int cn = c_axis<Q>(i, ax) * sgn;
+            const int ct = c_axis<Q>(i, tg);
             if (cn == 0 && ct != 0) {
-                float cu = L::cx(i) * ub[0] + L::cy(i) * ub[1] + L::cz(i) * ub[2];
-                float geq = L::w(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+                const float cu = cdot(L::cx(i), L::cy(i), L::cz(i), ubx, uby, ubz);
+                const float geq = L::w(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
                 nres += (g[i] - geq) * ct;
             }
             if (cn > 0) ncnt += ct * ct;
         }
-        float corr = nres / ncnt;
+        const float corr = nres / ncnt;
 #pragma unroll
         for (int i = 0; i < Q; ++i)
             if (c_axis<Q>(i, ax) * sgn > 0) g[i] -= c_axis<Q>(i, tg) * corr;
@@ -280,38 +374,37 @@ __device__ __forceinline__ void zou_he(const Params& P, float prof, float* g)
 
 // Extrapolation outlet (Sec. 4) with prescribed density: unknown populations
 // f_i = f_i^eq(rho_out, u_nb) + f_i(nb) - f_i^eq(rho_nb, u_nb), nb = y + n the
-// first interior neighbour along the inward normal n, pulled afresh.
+// first interior neighbour along the inward normal n, pulled afresh.  Two
+// passes over the neighbour's populations keep the register footprint small.
 template <int Q, class T>
 __device__ __forceinline__ void outlet(const Params& P, const Coords& c, float phi, uint32_t nbmask, float* g)
 {
     using L = Lattice<Q>;
     const int ax = P.out_axis;
     const int sgn = P.out_side == 1 ? -1 : 1;
-    int nx = c.x + (ax == 0 ? sgn : 0);
-    int ny = c.y + (ax == 1 ? sgn : 0);
-    int nz = c.z + (ax == 2 ? sgn : 0);
-    Coords nc = make_coords(P, nx, ny, nz);
-    float phin = P.phi[nc.idx];
-    float gn[Q];
-    pull<Q, T>(static_cast<const T*>(P.fsrc), P.N, nc, nbmask, gn);
+    const Coords nc = make_coords(P, c.x + (ax == 0 ? sgn : 0), c.y + (ax == 1 ? sgn : 0), c.z + (ax == 2 ? sgn : 0));
+    const float phin = __ldg(P.phi + nc.idx);
+    const T* f = static_cast<const T*>(P.fsrc);
     float sd = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        sd += gn[i];
-        mx += L::cx(i) * gn[i];
-        my += L::cy(i) * gn[i];
-        mz += L::cz(i) * gn[i];
+        const float v = Store<T>::ld(f + pull_offset<Q>(P.N, nc, nbmask, i));
+        sd += v;
+        if (L::cx(i)) mx += L::cx(i) > 0 ? v : -v;
+        if (L::cy(i)) my += L::cy(i) > 0 ? v : -v;
+        if (L::cz(i)) mz += L::cz(i) > 0 ? v : -v;
     }
-    Macro M = macroscopic(P, phin, sd, mx, my, mz);
-    float uu = M.ux * M.ux + M.uy * M.uy + M.uz * M.uz;
+    const Macro M = macroscopic(P, phin, sd, mx, my, mz);
+    const float uu = M.ux * M.ux + M.uy * M.uy + M.uz * M.uz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (c_axis<Q>(i, ax) * sgn > 0) {
-            float cu = L::cx(i) * M.ux + L::cy(i) * M.uy + L::cz(i) * M.uz;
-            float pe = 3.0f * cu + 4.5f * cu * cu - 1.5f * uu;
+            const float gn = Store<T>::ld(f + pull_offset<Q>(P.N, nc, nbmask, i));
+            const float cu = cdot(L::cx(i), L::cy(i), L::cz(i), M.ux, M.uy, M.uz);
+            const float pe = 3.0f * cu + 4.5f * cu * cu - 1.5f * uu;
             // (f^eq(rho_out) - w phi) + (g_nb + w phi_nb) - f^eq(rho_nb)
-            float w = L::w(i);
-            g[i] = w * phi * (P.rho_out - 1.0f + P.rho_out * pe) + gn[i] - w * phin * (M.drho + M.rho * pe);
+            const float w = L::w(i);
+            g[i] = w * phi * (P.rho_out - 1.0f + P.rho_out * pe) + gn - w * phin * (M.drho + M.rho * pe);
         }
     }
 }
@@ -353,129 +446,191 @@ __device__ __forceinline__ void block_reduce_diag(double* v, double* partials)
 // MODE kModeStep: full time step (pull, boundaries, moments, relaxation rate,
 // collision, store).  kModeMoments: pull + boundaries + moments and fields of
 // the current time.  kModeDiag: the same fields reduced to diagnostics.
-template <int Q, class T, int MODE>
-__global__ void __launch_bounds__(kBlock) lbm_kernel(const Params P)
+// One cell of the fused step / moments / diagnostics: list position p, its
+// dense index idx and link mask, fast or general path; diagnostics accumulate
+// into dv.
+// park: this thread's column of a Q x kBlock shared array (time step only).
+template <int Q, class T, int MODE, bool fast>
+__device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t idx, uint32_t mask, double* dv,
+                                          volatile float* park)
 {
     using L = Lattice<Q>;
-    const int p = blockIdx.x * kBlock + threadIdx.x;
-    double dv[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1e300, 0.0, 0.0};
-    // dv: 0 sum phi, 1 sum (phi rho - phi), 2 kinetic energy, 3 region sum |u|,
-    //     4 region count, 5 max |u|, 6 min omega, 7 max omega, 8 non-finite count
-    if (MODE == kModeDiag) dv[7] = -1e300;
-    if (p < P.n_cells) {
-        const uint32_t pc = P.cells[p];
-        const uint32_t mask = P.mask[p];
-        const Coords c = make_coords(P, pc & 1023u, (pc >> 10) & 1023u, pc >> 20);
-        const float phi = P.phi[c.idx];
-        float g[Q];
-        pull<Q, T>(static_cast<const T*>(P.fsrc), P.N, c, mask, g);
+    const float phi = __ldg(P.phi + idx);
+    const T* __restrict__ fs = static_cast<const T*>(P.fsrc);
+    const uint32_t N = (uint32_t)P.N;
+    const int sy = P.nx, sz = P.nx * P.ny;
+    float g[Q];
+    Coords cg;  // general path: wrapped neighbour coordinates of this cell
+    if (fast) {
+        // y - c_i never wraps here: index = idx - (c_x + c_y nx + c_z nx ny);
+        // element offsets fit 32 bits (the host routes larger boxes to the
+        // general path).
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const uint32_t d = (uint32_t)(L::cx(i) + L::cy(i) * sy + L::cz(i) * sz);
+            const uint32_t o = ((mask >> i) & 1u) ? (uint32_t)opp(i) * N + idx : (uint32_t)i * N + idx - d;
+            g[i] = Store<T>::ld(fs + o);
+        }
+    } else {
+        cg = coords_of(P, idx);
+        pull_general<Q, T>(fs, P.N, cg, mask, g);
         const int type = (mask >> kTypeShift) & 3u;
         if (type == kInlet) {
             zou_he<Q>(P, P.bnd_prof[p - P.n_bulk], g);
         } else if (type == kOutlet) {
-            outlet<Q, T>(P, c, phi, P.bnd_nbmask[p - P.n_bulk], g);
-        }
-        // moments: sum g, sum g c, sum g c c
-        float sd = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
-        float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-            const float v = g[i];
-            sd += v;
-            if (cx) mx += cx * v;
-            if (cy) my += cy * v;
-            if (cz) mz += cz * v;
-            if (cx) sxx += v;
-            if (cy) syy += v;
-            if (cz) szz += v;
-            if (cx * cy) sxy += (cx * cy) * v;
-            if (cx * cz) sxz += (cx * cz) * v;
-            if (cy * cz) syz += (cy * cz) * v;
-        }
-        const Macro M = macroscopic(P, phi, sd, mx, my, mz);
-        // corrected second moment Pi (Sec. 3), via sum f^eq c c = phi rho (c_s^2 I + u u)
-        const float cs2 = 1.0f / 3.0f;
-        const float pxx = sxx - M.sd * cs2 - M.sigma * M.ux * M.ux + M.Fx * M.ux;
-        const float pyy = syy - M.sd * cs2 - M.sigma * M.uy * M.uy + M.Fy * M.uy;
-        const float pzz = szz - M.sd * cs2 - M.sigma * M.uz * M.uz + M.Fz * M.uz;
-        const float pxy = sxy - M.sigma * M.ux * M.uy + 0.5f * (M.Fx * M.uy + M.ux * M.Fy);
-        const float pxz = sxz - M.sigma * M.ux * M.uz + 0.5f * (M.Fx * M.uz + M.ux * M.Fz);
-        const float pyz = syz - M.sigma * M.uy * M.uz + 0.5f * (M.Fy * M.uz + M.uy * M.Fz);
-        const float pn = sqrtf(pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz));
-        // semi-explicit shear rate gdot(t) = omega(t-1) ||Pi||_F / (c_s^2 rho)
-        const float om_prev = P.omega[p];
-        const float gdot = 3.0f * om_prev * pn / M.rho;
-        const float om = relaxation_rate(P, M.rho, gdot);
-
-        if (MODE == kModeStep) {
-            T* __restrict__ fd = static_cast<T*>(P.fdst);
-            const bool porous = (mask & kPorousBit) != 0u;
-            const float uu = M.ux * M.ux + M.uy * M.uy + M.uz * M.uz;
-            const float uF = M.ux * M.Fx + M.uy * M.Fy + M.uz * M.Fz;
-            const float h = 1.0f - 0.5f * om;
-            const float one_m_om = 1.0f - om;
-            // rest direction
-            {
-                const float w = L::w(0);
-                const float geq = w * (M.sd - 1.5f * M.sigma * uu);
-                const float gf = w * h * (-3.0f * uF);
-                Store<T>::st(fd + c.idx, one_m_om * g[0] + om * geq + gf);
-            }
-#pragma unroll
-            for (int i = 1; i < Q; i += 2) {
-                const int j = i + 1;
-                const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-                const float w = L::w(i);
-                const float cu = cx * M.ux + cy * M.uy + cz * M.uz;
-                const float cF = cx * M.Fx + cy * M.Fy + cz * M.Fz;
-                // f^eq - w phi split into even and odd parts in c
-                const float ev = w * (M.sd + M.sigma * (4.5f * cu * cu - 1.5f * uu));
-                const float od = 3.0f * w * M.sigma * cu;
-                // Guo forcing w (1 - omega/2)((c - u)/c_s^2 + (c.u) c / c_s^4) . F
-                const float fe = w * h * (9.0f * cu * cF - 3.0f * uF);
-                const float fo = 3.0f * w * h * cF;
-                float pi = 0.0f, pj = 0.0f;
-                if (porous) {
-                    // Omega^phi_i = w rho (phi(y + c_i) - phi(y)) in deviation form
-                    // (the stored reference moves to phi(y + c_i)): w (rho - 1) dphi.
-                    if (!((mask >> j) & 1u)) pi = w * M.drho * (P.phi[shifted(c, cx, cy, cz)] - phi);
-                    if (!((mask >> i) & 1u)) pj = w * M.drho * (P.phi[shifted(c, -cx, -cy, -cz)] - phi);
-                }
-                Store<T>::st(fd + (long long)i * P.N + c.idx, one_m_om * g[i] + om * (ev + od) + fe + fo + pi);
-                Store<T>::st(fd + (long long)j * P.N + c.idx, one_m_om * g[j] + om * (ev - od) + fe - fo + pj);
-            }
-            P.omega[p] = om;
-        } else if (MODE == kModeMoments) {
-            const long long o = P.o_compact ? (long long)p : c.idx;
-            if (P.o_rho) P.o_rho[o] = M.rho;
-            if (P.o_ux) P.o_ux[o] = M.ux;
-            if (P.o_uy) P.o_uy[o] = M.uy;
-            if (P.o_uz) P.o_uz[o] = M.uz;
-            if (P.o_gdot) P.o_gdot[o] = gdot;
-            if (P.o_omega) P.o_omega[o] = om;
-        } else {
-            const float un = sqrtf(M.ux * M.ux + M.uy * M.uy + M.uz * M.uz);
-            if (!isfinite(M.rho) || !isfinite(un) || !isfinite(om)) {
-                dv[8] = 1.0;
-            } else {
-                dv[0] = phi;
-                dv[1] = M.sd;
-                dv[2] = 0.5 * (double)M.rho * (double)un * (double)un;
-                if (P.region && P.region[c.idx]) {
-                    dv[3] = un;
-                    dv[4] = 1.0;
-                }
-                dv[5] = un;
-                dv[6] = om;
-                dv[7] = om;
-            }
+            outlet<Q, T>(P, cg, phi, P.bnd_nbmask[p - P.n_bulk], g);
         }
     }
-    if (MODE == kModeDiag) block_reduce_diag(dv, P.partials);
+    // The time step parks the pulled populations in this thread's column of
+    // shared memory: the moments below consume the register copies, and the
+    // collision re-reads them from shared memory, so the Q values need not stay
+    // in registers through the macroscopic, shear-rate and viscosity phase.
+    if (MODE == kModeStep) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) park[i * kBlock] = g[i];
+    }
+    const Moments<Q> m = moments<Q>(g);
+    const Macro M = macroscopic(P, phi, m.sd, m.mx, m.my, m.mz);
+    // corrected second moment Pi (Sec. 3), via sum f^eq c c = phi rho (c_s^2 I + u u)
+    const float sd3 = M.sd * (1.0f / 3.0f);
+    const float pxx = fmaf(M.ux, fmaf(-M.sigma, M.ux, M.Fx), m.sxx - sd3);
+    const float pyy = fmaf(M.uy, fmaf(-M.sigma, M.uy, M.Fy), m.syy - sd3);
+    const float pzz = fmaf(M.uz, fmaf(-M.sigma, M.uz, M.Fz), m.szz - sd3);
+    const float pxy = fmaf(M.ux, fmaf(-M.sigma, M.uy, 0.5f * M.Fy), fmaf(0.5f * M.Fx, M.uy, m.sxy));
+    const float pxz = fmaf(M.ux, fmaf(-M.sigma, M.uz, 0.5f * M.Fz), fmaf(0.5f * M.Fx, M.uz, m.sxz));
+    const float pyz = fmaf(M.uy, fmaf(-M.sigma, M.uz, 0.5f * M.Fz), fmaf(0.5f * M.Fy, M.uz, m.syz));
+    const float pn2 = fmaf(pxx, pxx, fmaf(pyy, pyy, fmaf(pzz, pzz, 2.0f * fmaf(pxy, pxy, fmaf(pxz, pxz, pyz * pyz)))));
+    // semi-explicit shear rate gdot(t) = omega(t-1) ||Pi||_F / (c_s^2 rho)
+    const float om_prev = P.omega[p];
+    const float gdot = __fdividef(3.0f * om_prev * sqrtf(pn2), M.rho);
+    const float om = relaxation_rate(P, M.rho, gdot);
+
+    if (MODE == kModeStep) {
+        T* __restrict__ fd = static_cast<T*>(P.fdst);
+        const bool porous = (mask & kPorousBit) != 0u;
+        const float uu = fmaf(M.ux, M.ux, fmaf(M.uy, M.uy, M.uz * M.uz));
+        const float uF = fmaf(M.ux, M.Fx, fmaf(M.uy, M.Fy, M.uz * M.Fz));
+        const float h = fmaf(-0.5f, om, 1.0f);
+        const float omo = 1.0f - om;
+        // Per unit weight: even part omega (f^eq - w phi) + Guo even part,
+        // coefficients of (c.u)^2 and (c.u)(c.F), odd coefficients of c.u and c.F.
+        const float e0 = fmaf(om, fmaf(-1.5f * M.sigma, uu, M.sd), -3.0f * h * uF);
+        const float ek = 4.5f * om * M.sigma;
+        const float gk = 9.0f * h;
+        const float os = 3.0f * om * M.sigma;
+        const float of = 3.0f * h;
+        T* __restrict__ dp = fd + idx;  // this cell in plane 0; plane i at + i N
+        {
+            const float w = L::w(0);
+            Store<T>::st(dp, fmaf(omo, park[0], w * e0));
+        }
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const int j = i + 1;
+            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            const float w = L::w(i);
+            const float cu = cdot(cx, cy, cz, M.ux, M.uy, M.uz);
+            const float cF = cdot(cx, cy, cz, M.Fx, M.Fy, M.Fz);
+            // f^eq - w phi = w (sd + sigma (3 cu + 4.5 cu^2 - 1.5 uu)); Guo:
+            // w (1 - omega/2)(3 cF - 3 uF + 9 cu cF)
+            const float ev = w * fmaf(cu * cu, ek, fmaf(cu * cF, gk, e0));
+            const float od = w * fmaf(cu, os, cF * of);
+            float vi = fmaf(omo, park[i * kBlock], ev + od);
+            float vj = fmaf(omo, park[j * kBlock], ev - od);
+            if (porous) {
+                // Omega^phi_i = w rho (phi(y + c_i) - phi(y)) in deviation form
+                // (the stored reference moves to phi(y + c_i)): w (rho - 1) dphi.
+                // A set mask bit means that neighbour is solid or outside: the
+                // cell reads its own porosity there, so dphi = 0 without a branch.
+                const uint32_t d = (uint32_t)(cx + cy * sy + cz * sz);
+                const float wd = w * M.drho;
+                uint32_t ni, nj;
+                if (fast) {
+                    ni = ((mask >> j) & 1u) ? idx : idx + d;
+                    nj = ((mask >> i) & 1u) ? idx : idx - d;
+                } else {
+                    ni = ((mask >> j) & 1u) ? idx : (uint32_t)shifted(cg, cx, cy, cz);
+                    nj = ((mask >> i) & 1u) ? idx : (uint32_t)shifted(cg, -cx, -cy, -cz);
+                }
+                vi = fmaf(wd, __ldg(P.phi + ni) - phi, vi);
+                vj = fmaf(wd, __ldg(P.phi + nj) - phi, vj);
+            }
+            Store<T>::st(dp + (size_t)i * P.N, vi);
+            Store<T>::st(dp + (size_t)j * P.N, vj);
+        }
+        P.omega[p] = om;
+    } else if (MODE == kModeMoments) {
+        const long long o = P.o_compact ? (long long)p : (long long)idx;
+        if (P.o_rho) P.o_rho[o] = M.rho;
+        if (P.o_ux) P.o_ux[o] = M.ux;
+        if (P.o_uy) P.o_uy[o] = M.uy;
+        if (P.o_uz) P.o_uz[o] = M.uz;
+        if (P.o_gdot) P.o_gdot[o] = gdot;
+        if (P.o_omega) P.o_omega[o] = om;
+    } else {
+        const float un = sqrtf(M.ux * M.ux + M.uy * M.uy + M.uz * M.uz);
+        if (!isfinite(M.rho) || !isfinite(un) || !isfinite(om)) {
+            dv[8] = 1.0;
+        } else {
+            dv[0] = phi;
+            dv[1] = M.sd;
+            dv[2] = 0.5 * (double)M.rho * (double)un * (double)un;
+            if (P.region && P.region[idx]) {
+                dv[3] = un;
+                dv[4] = 1.0;
+            }
+            dv[5] = un;
+            dv[6] = om;
+            dv[7] = om;
+        }
+    }
 }
 
-// Final deterministic reduction of the per-block diagnostics (one block).
-__global__ void diag_finish(const double* __restrict__ partials, int nblk, double* __restrict__ out);
+// Cells of the general path (periodic wrap, inlet, outlet) in a function of
+// their own, so that their register needs do not bound the fast path.
+template <int Q, class T, int MODE>
+__device__ __noinline__ void cell_general(const Params& P, int p, uint32_t idx, uint32_t mask, double* dv,
+                                          volatile float* park)
+{
+    cell_impl<Q, T, MODE, false>(P, p, idx, mask, dv, park);
+}
+
+template <int Q, class T, int MODE>
+__device__ __forceinline__ void cell_body(const Params& P, int p, uint32_t idx, uint32_t mask, bool fast, double* dv,
+                                          volatile float* park)
+{
+    if (fast)
+        cell_impl<Q, T, MODE, true>(P, p, idx, mask, dv, park);
+    else
+        cell_general<Q, T, MODE>(P, p, idx, mask, dv, park);
+}
+
+// Shared column for parking the pulled populations during a time step.
+template <int Q, int MODE>
+__device__ __forceinline__ volatile float* park_column()
+{
+    if (MODE != kModeStep) return nullptr;
+    __shared__ float sg[Q * kBlock];
+    return sg + threadIdx.x;
+}
+
+// MODE kModeStep: full time step (pull, boundaries, moments, relaxation rate,
+// collision, store).  kModeMoments: pull + boundaries + moments and fields of
+// the current time.  kModeDiag: the same fields reduced to diagnostics.
+template <int Q, class T, int MODE>
+__global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS) lbm_kernel(const Params P)
+{
+    const int nbg = general_blocks(P);
+    const bool fast = (int)blockIdx.x >= nbg;
+    const int p = fast ? ((int)blockIdx.x - nbg) * kBlock + (int)threadIdx.x
+                       : P.n_fast + (int)blockIdx.x * kBlock + (int)threadIdx.x;
+    const int pend = fast ? P.n_fast : P.n_cells;
+    double dv[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1e300, -1e300, 0.0};
+    // dv: 0 sum phi, 1 sum (phi rho - phi), 2 kinetic energy, 3 region sum |u|,
+    //     4 region count, 5 max |u|, 6 min omega, 7 max omega, 8 non-finite count
+    volatile float* park = park_column<Q, MODE>();
+    if (p < pend) cell_body<Q, T, MODE>(P, p, P.cells[p], P.mask[p], fast, dv, park);
+    if (MODE == kModeDiag) block_reduce_diag(dv, P.partials);
+}
 
 }  // namespace lbm

@@ -56,4 +56,13 @@ __host__ __device__ constexpr int c_axis(int i, int a)
     return a == 0 ? Lattice<Q>::cx(i) : a == 1 ? Lattice<Q>::cy(i) : Lattice<Q>::cz(i);
 }
 
+// Index of the direction (cx, cy, cz) in the Q-velocity set, -1 if absent.
+template <int Q>
+__host__ __device__ constexpr int find_dir(int cx, int cy, int cz)
+{
+    for (int i = 0; i < Q; ++i)
+        if (Lattice<Q>::cx(i) == cx && Lattice<Q>::cy(i) == cy && Lattice<Q>::cz(i) == cz) return i;
+    return -1;
+}
+
 }  // namespace lbm

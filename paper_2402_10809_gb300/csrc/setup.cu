@@ -12,7 +12,22 @@
 
 namespace lbm {
 
-__device__ __forceinline__ int category(uint8_t f) { return f == 1 ? 0 : f == 2 ? 1 : f == 3 ? 2 : -1; }
+// List group of a cell: 0 bulk off periodic faces, 1 bulk on a periodic face,
+// 2 inlet, 3 outlet, -1 solid.
+__device__ __forceinline__ int category(uint8_t f, long long idx, const CellGrid& G)
+{
+    if (f == 2) return 2;
+    if (f == 3) return 3;
+    if (f != 1) return -1;
+    const long long plane = (long long)G.nx * G.ny;
+    const int z = (int)(idx / plane);
+    const long long r = idx - (long long)z * plane;
+    const int y = (int)(r / G.nx);
+    const int x = (int)(r - (long long)y * G.nx);
+    const bool wrap = (G.periodic[0] && (x == 0 || x == G.nx - 1)) || (G.periodic[1] && (y == 0 || y == G.ny - 1)) ||
+                      (G.periodic[2] && (z == 0 || z == G.nz - 1));
+    return wrap ? 1 : 0;
+}
 
 // Inclusive scan over a 256-thread block; returns the exclusive prefix and the
 // block total.
@@ -38,31 +53,32 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
     return base + x - v;
 }
 
-__global__ void setup_count(const uint8_t* __restrict__ flags, long long N, int nblk, uint32_t* __restrict__ counts)
+__global__ void setup_count(const uint8_t* __restrict__ flags, long long N, CellGrid G, int nblk,
+                            uint32_t* __restrict__ counts)
 {
     const long long base = (long long)blockIdx.x * kSetupChunk + (long long)threadIdx.x * kSetupCellsPerThread;
-    uint32_t c[3] = {0, 0, 0};
+    uint32_t c[kCategories] = {0, 0, 0, 0};
     for (int k = 0; k < kSetupCellsPerThread; ++k) {
         const long long idx = base + k;
         if (idx < N) {
-            const int cat = category(flags[idx]);
+            const int cat = category(flags[idx], idx, G);
             if (cat >= 0) c[cat] += 1;
         }
     }
-    for (int cat = 0; cat < 3; ++cat) {
+    for (int cat = 0; cat < kCategories; ++cat) {
         uint32_t tot;
         block_exclusive_scan(c[cat], &tot);
         if (threadIdx.x == 0) counts[cat * nblk + blockIdx.x] = tot;
     }
 }
 
-// One block: exclusive scan of counts[3 * nblk] (category-major) into offsets,
-// and the category totals.
+// One block: exclusive scan of counts[kCategories * nblk] (category-major) into
+// offsets, and the category totals.
 __global__ void setup_scan(const uint32_t* __restrict__ counts, int nblk, uint32_t* __restrict__ offsets,
                            uint32_t* __restrict__ totals)
 {
     __shared__ uint32_t part[1024];
-    const int n = 3 * nblk;
+    const int n = kCategories * nblk;
     const int per = (n + 1023) / 1024;
     const int lo = threadIdx.x * per;
     const int hi = min(n, lo + per);
@@ -86,7 +102,7 @@ __global__ void setup_scan(const uint32_t* __restrict__ counts, int nblk, uint32
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int cat = 0; cat < 3; ++cat) {
+        for (int cat = 0; cat < kCategories; ++cat) {
             uint32_t t = 0;
             for (int b = 0; b < nblk; ++b) t += counts[cat * nblk + b];
             totals[cat] = t;
@@ -94,35 +110,28 @@ __global__ void setup_scan(const uint32_t* __restrict__ counts, int nblk, uint32
     }
 }
 
-__global__ void setup_emit(const uint8_t* __restrict__ flags, long long N, int nx, int ny, int nblk,
+__global__ void setup_emit(const uint8_t* __restrict__ flags, long long N, CellGrid G, int nblk,
                            const uint32_t* __restrict__ offsets, uint32_t* __restrict__ cells)
 {
     const long long base = (long long)blockIdx.x * kSetupChunk + (long long)threadIdx.x * kSetupCellsPerThread;
-    uint32_t c[3] = {0, 0, 0};
+    uint32_t c[kCategories] = {0, 0, 0, 0};
     for (int k = 0; k < kSetupCellsPerThread; ++k) {
         const long long idx = base + k;
         if (idx < N) {
-            const int cat = category(flags[idx]);
+            const int cat = category(flags[idx], idx, G);
             if (cat >= 0) c[cat] += 1;
         }
     }
-    uint32_t pos[3];
-    for (int cat = 0; cat < 3; ++cat) {
+    uint32_t pos[kCategories];
+    for (int cat = 0; cat < kCategories; ++cat) {
         uint32_t tot;
         pos[cat] = offsets[cat * nblk + blockIdx.x] + block_exclusive_scan(c[cat], &tot);
     }
-    const long long plane = (long long)nx * ny;
     for (int k = 0; k < kSetupCellsPerThread; ++k) {
         const long long idx = base + k;
         if (idx < N) {
-            const int cat = category(flags[idx]);
-            if (cat >= 0) {
-                const uint32_t z = (uint32_t)(idx / plane);
-                const long long r = idx - (long long)z * plane;
-                const uint32_t y = (uint32_t)(r / nx);
-                const uint32_t x = (uint32_t)(r - (long long)y * nx);
-                cells[pos[cat]++] = x | (y << 10) | (z << 20);
-            }
+            const int cat = category(flags[idx], idx, G);
+            if (cat >= 0) cells[pos[cat]++] = (uint32_t)idx;
         }
     }
 }
@@ -159,6 +168,9 @@ __device__ uint32_t link_mask(const SetupParams& S, int x, int y, int z, int typ
     const long long idx = x + (long long)S.nx * (y + (long long)S.ny * z);
     const float phi = S.phi[idx];
     uint32_t m = (uint32_t)type << kTypeShift;
+    if ((S.periodic[0] && (x == 0 || x == S.nx - 1)) || (S.periodic[1] && (y == 0 || y == S.ny - 1)) ||
+        (S.periodic[2] && (z == 0 || z == S.nz - 1)))
+        m |= kWrapBit;
     for (int i = 0; i < Q; ++i) {
         long long s;
         int ax, sd;
@@ -179,8 +191,11 @@ __global__ void setup_mask(const SetupParams S)
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= S.n_cells) return;
     const uint32_t pc = S.cells[p];
-    const int x = pc & 1023u, y = (pc >> 10) & 1023u, z = pc >> 20;
-    const long long idx = x + (long long)S.nx * (y + (long long)S.ny * z);
+    const long long idx = pc;
+    const long long plane = (long long)S.nx * S.ny;
+    const int z = (int)(idx / plane);
+    const int y = (int)((idx - (long long)z * plane) / S.nx);
+    const int x = (int)(idx - (long long)z * plane - (long long)y * S.nx);
     const uint8_t fl = S.flags[idx];
     const float phi = S.phi[idx];
     uint32_t err = 0;
@@ -252,8 +267,7 @@ __global__ void init_state(const uint32_t* __restrict__ cells, int n_cells, int 
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_cells) return;
-    const uint32_t pc = cells[p];
-    const long long idx = (pc & 1023u) + (long long)nx * (((pc >> 10) & 1023u) + (long long)ny * (pc >> 20));
+    const long long idx = cells[p];
     for (int i = 0; i < Q; ++i) f[(long long)i * N + idx] = T(0.0f);
     omega[p] = omega0;
 }
@@ -266,8 +280,7 @@ __global__ void pack_state(const uint32_t* __restrict__ cells, int n_cells, int 
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_cells) return;
-    const uint32_t pc = cells[p];
-    const long long idx = (pc & 1023u) + (long long)nx * (((pc >> 10) & 1023u) + (long long)ny * (pc >> 20));
+    const long long idx = cells[p];
     if (unpack) {
         for (int i = 0; i < Q; ++i) fout[(long long)i * N + idx] = state_in[(long long)i * n_cells + p];
     } else {
@@ -361,15 +374,15 @@ cudaError_t launch_pack_state(int storage, const uint32_t* cells, int n_cells, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_setup_cells(const uint8_t* flags, long long N, int nx, int ny, uint32_t* counts,
+cudaError_t launch_setup_cells(const uint8_t* flags, long long N, const CellGrid& G, uint32_t* counts,
                                uint32_t* offsets, uint32_t* totals, cudaStream_t s, int phase, uint32_t* cells)
 {
     const int nblk = (int)((N + kSetupChunk - 1) / kSetupChunk);
     if (phase == 0) {
-        setup_count<<<nblk, kSetupThreads, 0, s>>>(flags, N, nblk, counts);
+        setup_count<<<nblk, kSetupThreads, 0, s>>>(flags, N, G, nblk, counts);
         setup_scan<<<1, 1024, 0, s>>>(counts, nblk, offsets, totals);
     } else {
-        setup_emit<<<nblk, kSetupThreads, 0, s>>>(flags, N, nx, ny, nblk, offsets, cells);
+        setup_emit<<<nblk, kSetupThreads, 0, s>>>(flags, N, G, nblk, offsets, cells);
     }
     return cudaGetLastError();
 }

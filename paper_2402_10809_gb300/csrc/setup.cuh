@@ -11,6 +11,7 @@ namespace lbm {
 constexpr int kSetupThreads = 256;
 constexpr int kSetupCellsPerThread = 16;
 constexpr int kSetupChunk = kSetupThreads * kSetupCellsPerThread;
+constexpr int kCategories = 4;
 
 // Error bits raised by setup_mask.
 constexpr uint32_t kErrPorosity = 1u;  // porosity outside (0, 1] on a non-solid cell
@@ -34,8 +35,14 @@ struct SetupParams {
 };
 
 // Host launchers (setup.cu).  phase 0 of launch_setup_cells counts and scans,
-// phase 1 emits the list.
-cudaError_t launch_setup_cells(const uint8_t* flags, long long N, int nx, int ny, uint32_t* counts,
+// phase 1 emits the list of dense cell indices in four consecutive groups:
+// bulk cells away from periodic faces, bulk cells on a periodic face, inlet
+// cells, outlet cells (totals[0..3]).
+struct CellGrid {
+    int nx, ny, nz;
+    int periodic[3];
+};
+cudaError_t launch_setup_cells(const uint8_t* flags, long long N, const CellGrid& G, uint32_t* counts,
                                uint32_t* offsets, uint32_t* totals, cudaStream_t s, int phase, uint32_t* cells);
 cudaError_t launch_setup_mask(int q, const SetupParams& S, cudaStream_t s);
 cudaError_t launch_init_state(int storage, const uint32_t* cells, int n_cells, int nx, int ny, long long N, int Q,

@@ -31,7 +31,7 @@ namespace lbm {
 
 cudaError_t LBM_LAUNCHER(int mode, const Params& P, cudaStream_t s)
 {
-    const int grid = (P.n_cells + kBlock - 1) / kBlock;
+    const int grid = total_blocks(P);
     if (grid == 0) return cudaSuccess;
     switch (mode) {
         case kModeStep: lbm_kernel<LBM_Q, LBM_T, kModeStep><<<grid, kBlock, 0, s>>>(P); break;
