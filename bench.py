@@ -235,7 +235,7 @@ def run_ours(args):
         pin_reg = torch.from_numpy(np.ascontiguousarray(prob.region)).pin_memory()
         grid = lbm.make_grid(prob.dims, prob.q, "f32", prob.periodic)
         r, p, b = lbm.make_params(prob.rheology, prob.porous, prob.bc)
-        nbytes = lbm.lbm_workspace_size(grid, nf)
+        nbytes = lbm.lbm_workspace_size(grid, lbm.lbm_list_length(grid, pin_flags.data_ptr()))
         wsb = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         sh = stream.cuda_stream
 

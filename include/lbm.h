@@ -97,9 +97,14 @@ typedef struct {
     double rho_out;
 } lbm_bc;
 
-/* Bytes of device workspace for a grid holding n_fluid non-solid cells
- * (pass n_fluid < 0 for the bound n_fluid = nx*ny*nz).  0 on a bad grid. */
-size_t lbm_workspace_size(const lbm_grid* grid, int64_t n_fluid);
+/* Length of the internal cell list for these flags (host memory): every
+ * non-solid cell plus the solid cells that share an aligned 16-cell group with
+ * a bulk fluid cell (those receive full-sector zero stores).  -1 on bad input. */
+int64_t lbm_list_length(const lbm_grid* grid, const uint8_t* flags);
+
+/* Bytes of device workspace for a cell list of n_list entries (from
+ * lbm_list_length; pass n_list < 0 for the bound nx*ny*nz).  0 on a bad grid. */
+size_t lbm_workspace_size(const lbm_grid* grid, int64_t n_list);
 
 /* Creates a context and sets the initial state (Sec. 3, Sec. 4):
  * f_i = f_i^eq(rho = 1, u = 0) = w_i phi, omega = omega(mu0) at rho = 1, and

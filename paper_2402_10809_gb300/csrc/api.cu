@@ -65,9 +65,9 @@ Layout layout(const lbm_grid* g, long long nf)
     L.phi = take((size_t)N * 4);
     L.flags = take((size_t)N);
     L.region = take((size_t)N);
-    L.counts = take((size_t)nblk * kCategories * 4);
+    L.counts = take((size_t)nblk * kCounters * 4);
     L.offsets = take((size_t)nblk * kCategories * 4);
-    L.totals = take(16);
+    L.totals = take(kCounters * 4);
     L.err = take(32);
     L.diag_out = take(8 * 8);
     L.fixed_end = o;
@@ -109,6 +109,7 @@ struct lbm_ctx {
     Layout L{};
     long long N = 0;
     int n_cells = 0, n_fast = 0, n_bulk = 0, n_in = 0, n_out = 0;
+    int n_ghost = 0;  // ghost entries among the n_fast cells of group 0
     int cur = 0;
     long long t = 0;
     int check_every = 0;
@@ -141,11 +142,40 @@ static lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where)
         if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
     } while (0)
 
-extern "C" size_t lbm_workspace_size(const lbm_grid* grid, int64_t n_fluid)
+extern "C" size_t lbm_workspace_size(const lbm_grid* grid, int64_t n_list)
 {
     if (!grid_ok(grid)) return 0;
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
-    return layout(grid, n_fluid < 0 ? N : (n_fluid > N ? N : n_fluid)).end;
+    return layout(grid, n_list < 0 ? N : (n_list > N ? N : n_list)).end;
+}
+
+// Host mirror of the set-up's list rule: every non-solid cell, plus each solid
+// cell of an aligned 16-cell group that holds a bulk cell off periodic faces.
+extern "C" int64_t lbm_list_length(const lbm_grid* grid, const uint8_t* flags)
+{
+    if (!grid_ok(grid) || !flags) return -1;
+    const long long nx = grid->nx, ny = grid->ny, nz = grid->nz, N = nx * ny * nz;
+    auto periodic_face = [&](long long idx) {
+        const long long z = idx / (nx * ny), r = idx - z * nx * ny, y = r / nx, x = r - y * nx;
+        return (grid->periodic[0] && (x == 0 || x == nx - 1)) || (grid->periodic[1] && (y == 0 || y == ny - 1)) ||
+               (grid->periodic[2] && (z == 0 || z == nz - 1));
+    };
+    int64_t n = 0;
+    for (long long g0 = 0; g0 < N; g0 += kGhostGroup) {
+        const long long g1 = g0 + kGhostGroup < N ? g0 + kGhostGroup : N;
+        bool bulk = false;
+        int64_t listed = 0, solid = 0;
+        for (long long i = g0; i < g1; ++i) {
+            if (flags[i] == LBM_SOLID) {
+                ++solid;
+            } else if (flags[i] <= LBM_OUTLET) {
+                ++listed;
+                if (flags[i] == LBM_FLUID && !bulk && !periodic_face(i)) bulk = true;
+            }
+        }
+        n += listed + (bulk ? solid : 0);
+    }
+    return n;
 }
 
 static lbm_status run_diag(lbm_ctx* c, const uint8_t* region_dev, double out[8])
@@ -212,7 +242,7 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     LBM_CUDA(launch_setup_cells(c->at<uint8_t>(c->L.flags), c->N, CG, c->at<uint32_t>(c->L.counts),
                                 c->at<uint32_t>(c->L.offsets), c->at<uint32_t>(c->L.totals), c->stream, 0, nullptr),
              "setup count");
-    uint32_t tot[kCategories] = {0, 0, 0, 0};
+    uint32_t tot[kCounters] = {0, 0, 0, 0, 0};
     LBM_CUDA(cudaMemcpyAsync(tot, c->at<uint32_t>(c->L.totals), sizeof(tot), cudaMemcpyDeviceToHost, c->stream),
              "copy totals");
     LBM_CUDA(cudaStreamSynchronize(c->stream), "setup sync");
@@ -220,10 +250,12 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     c->n_bulk = (int)(tot[0] + tot[1]);
     c->n_in = (int)tot[2];
     c->n_out = (int)tot[3];
+    c->n_ghost = (int)tot[4];
     c->n_cells = c->n_bulk + c->n_in + c->n_out;
     c->L = layout(grid, c->n_cells);
     if (workspace_bytes < c->L.end)
-        return fail(c, LBM_ENOMEM, "workspace smaller than lbm_workspace_size(grid, " + std::to_string(c->n_cells) + ")");
+        return fail(c, LBM_ENOMEM, "workspace smaller than lbm_workspace_size(grid, " + std::to_string(c->n_cells) +
+                                       "), the cell-list length of these flags");
     LBM_CUDA(launch_setup_cells(c->at<uint8_t>(c->L.flags), c->N, CG, c->at<uint32_t>(c->L.counts),
                                 c->at<uint32_t>(c->L.offsets), c->at<uint32_t>(c->L.totals), c->stream, 1,
                                 c->at<uint32_t>(c->L.cells)),
@@ -408,7 +440,8 @@ extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho, float* u, float* shear
     for (int k = 0; k < 6; ++k) {
         if (!outs[k]) continue;
         std::memset(outs[k], 0, N * 4);
-        for (size_t p = 0; p < n; ++p) outs[k][c->host_cells[p]] = h[k * n + p];
+        for (size_t p = 0; p < n; ++p)
+            if (!(c->host_cells[p] & kGhostFlag)) outs[k][c->host_cells[p]] = h[k * n + p];
     }
     return LBM_OK;
 }
@@ -517,7 +550,7 @@ extern "C" lbm_status lbm_load(lbm_ctx* c, const void* src, size_t bytes, int32_
 }
 
 extern "C" int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
-extern "C" int64_t lbm_fluid_count(const lbm_ctx* c) { return c ? c->n_cells : -1; }
+extern "C" int64_t lbm_fluid_count(const lbm_ctx* c) { return c ? c->n_cells - c->n_ghost : -1; }
 extern "C" const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
 extern "C" void lbm_destroy(lbm_ctx* c) { delete c; }
 

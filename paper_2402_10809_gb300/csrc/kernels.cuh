@@ -455,6 +455,16 @@ __device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t idx, 
                                           volatile float* park)
 {
     using L = Lattice<Q>;
+    if (fast && (idx & 0x80000000u)) {
+        // ghost entry (a solid cell sharing a 16-cell group with bulk cells):
+        // complete this cell's sectors with zeros; nothing reads them.
+        if (MODE == kModeStep) {
+            T* __restrict__ gd = static_cast<T*>(P.fdst) + (idx & 0x7fffffffu);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) Store<T>::st(gd + (size_t)i * P.N, 0.0f);
+        }
+        return;
+    }
     const float phi = __ldg(P.phi + idx);
     const T* __restrict__ fs = static_cast<const T*>(P.fsrc);
     const uint32_t N = (uint32_t)P.N;

@@ -12,21 +12,36 @@
 
 namespace lbm {
 
-// List group of a cell: 0 bulk off periodic faces, 1 bulk on a periodic face,
-// 2 inlet, 3 outlet, -1 solid.
-__device__ __forceinline__ int category(uint8_t f, long long idx, const CellGrid& G)
+__device__ __forceinline__ bool on_periodic_face(long long idx, const CellGrid& G)
 {
-    if (f == 2) return 2;
-    if (f == 3) return 3;
-    if (f != 1) return -1;
     const long long plane = (long long)G.nx * G.ny;
     const int z = (int)(idx / plane);
     const long long r = idx - (long long)z * plane;
     const int y = (int)(r / G.nx);
     const int x = (int)(r - (long long)y * G.nx);
-    const bool wrap = (G.periodic[0] && (x == 0 || x == G.nx - 1)) || (G.periodic[1] && (y == 0 || y == G.ny - 1)) ||
-                      (G.periodic[2] && (z == 0 || z == G.nz - 1));
-    return wrap ? 1 : 0;
+    return (G.periodic[0] && (x == 0 || x == G.nx - 1)) || (G.periodic[1] && (y == 0 || y == G.ny - 1)) ||
+           (G.periodic[2] && (z == 0 || z == G.nz - 1));
+}
+
+// List group of a cell: 0 bulk off periodic faces (and ghosts, see setup.cuh),
+// 1 bulk on a periodic face, 2 inlet, 3 outlet, -1 not listed.
+__device__ __forceinline__ int category(uint8_t f, long long idx, const CellGrid& G, bool group_has_bulk)
+{
+    if (f == 2) return 2;
+    if (f == 3) return 3;
+    if (f == 0) return group_has_bulk ? 0 : -1;
+    if (f != 1) return -1;
+    return on_periodic_face(idx, G) ? 1 : 0;
+}
+
+// Whether the ghost group of this thread's cells holds a bulk cell of group 0.
+__device__ __forceinline__ bool group_has_bulk(const uint8_t* flags, long long base, long long N, const CellGrid& G)
+{
+    for (int k = 0; k < kSetupCellsPerThread; ++k) {
+        const long long idx = base + k;
+        if (idx < N && flags[idx] == 1 && !on_periodic_face(idx, G)) return true;
+    }
+    return false;
 }
 
 // Inclusive scan over a 256-thread block; returns the exclusive prefix and the
@@ -57,15 +72,17 @@ __global__ void setup_count(const uint8_t* __restrict__ flags, long long N, Cell
                             uint32_t* __restrict__ counts)
 {
     const long long base = (long long)blockIdx.x * kSetupChunk + (long long)threadIdx.x * kSetupCellsPerThread;
-    uint32_t c[kCategories] = {0, 0, 0, 0};
+    const bool gb = group_has_bulk(flags, base, N, G);
+    uint32_t c[kCounters] = {0, 0, 0, 0, 0};
     for (int k = 0; k < kSetupCellsPerThread; ++k) {
         const long long idx = base + k;
         if (idx < N) {
-            const int cat = category(flags[idx], idx, G);
+            const int cat = category(flags[idx], idx, G, gb);
             if (cat >= 0) c[cat] += 1;
+            if (cat == 0 && flags[idx] == 0) c[kCategories] += 1;
         }
     }
-    for (int cat = 0; cat < kCategories; ++cat) {
+    for (int cat = 0; cat < kCounters; ++cat) {
         uint32_t tot;
         block_exclusive_scan(c[cat], &tot);
         if (threadIdx.x == 0) counts[cat * nblk + blockIdx.x] = tot;
@@ -102,7 +119,7 @@ __global__ void setup_scan(const uint32_t* __restrict__ counts, int nblk, uint32
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int cat = 0; cat < kCategories; ++cat) {
+        for (int cat = 0; cat < kCounters; ++cat) {
             uint32_t t = 0;
             for (int b = 0; b < nblk; ++b) t += counts[cat * nblk + b];
             totals[cat] = t;
@@ -114,11 +131,12 @@ __global__ void setup_emit(const uint8_t* __restrict__ flags, long long N, CellG
                            const uint32_t* __restrict__ offsets, uint32_t* __restrict__ cells)
 {
     const long long base = (long long)blockIdx.x * kSetupChunk + (long long)threadIdx.x * kSetupCellsPerThread;
+    const bool gb = group_has_bulk(flags, base, N, G);
     uint32_t c[kCategories] = {0, 0, 0, 0};
     for (int k = 0; k < kSetupCellsPerThread; ++k) {
         const long long idx = base + k;
         if (idx < N) {
-            const int cat = category(flags[idx], idx, G);
+            const int cat = category(flags[idx], idx, G, gb);
             if (cat >= 0) c[cat] += 1;
         }
     }
@@ -130,8 +148,8 @@ __global__ void setup_emit(const uint8_t* __restrict__ flags, long long N, CellG
     for (int k = 0; k < kSetupCellsPerThread; ++k) {
         const long long idx = base + k;
         if (idx < N) {
-            const int cat = category(flags[idx], idx, G);
-            if (cat >= 0) cells[pos[cat]++] = (uint32_t)idx;
+            const int cat = category(flags[idx], idx, G, gb);
+            if (cat >= 0) cells[pos[cat]++] = (uint32_t)idx | (flags[idx] == 0 ? kGhostFlag : 0u);
         }
     }
 }
@@ -191,6 +209,10 @@ __global__ void setup_mask(const SetupParams S)
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= S.n_cells) return;
     const uint32_t pc = S.cells[p];
+    if (pc & kGhostFlag) {
+        S.mask[p] = kGhostFlag;
+        return;
+    }
     const long long idx = pc;
     const long long plane = (long long)S.nx * S.ny;
     const int z = (int)(idx / plane);
@@ -267,7 +289,7 @@ __global__ void init_state(const uint32_t* __restrict__ cells, int n_cells, int 
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_cells) return;
-    const long long idx = cells[p];
+    const long long idx = cells[p] & ~kGhostFlag;
     for (int i = 0; i < Q; ++i) f[(long long)i * N + idx] = T(0.0f);
     omega[p] = omega0;
 }
@@ -280,7 +302,7 @@ __global__ void pack_state(const uint32_t* __restrict__ cells, int n_cells, int 
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_cells) return;
-    const long long idx = cells[p];
+    const long long idx = cells[p] & ~kGhostFlag;
     if (unpack) {
         for (int i = 0; i < Q; ++i) fout[(long long)i * N + idx] = state_in[(long long)i * n_cells + p];
     } else {

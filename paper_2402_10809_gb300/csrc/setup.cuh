@@ -11,7 +11,16 @@ namespace lbm {
 constexpr int kSetupThreads = 256;
 constexpr int kSetupCellsPerThread = 16;
 constexpr int kSetupChunk = kSetupThreads * kSetupCellsPerThread;
-constexpr int kCategories = 4;
+constexpr int kCategories = 4;  // list groups: bulk, bulk on a periodic face, inlet, outlet
+constexpr int kCounters = 5;    // the four group sizes and the number of ghost entries (part of group 0)
+// Ghost entries: solid cells that share an aligned group of kGhostGroup cells
+// with a bulk cell.  They sit in group 0 in index order and only store zeros
+// into their (never read) distribution slots, so that every 32-byte sector a
+// warp writes is written whole and the memory never has to merge a partial
+// sector.  Marked by bit 31 of their cell-list entry.
+constexpr int kGhostGroup = 16;
+constexpr uint32_t kGhostFlag = 0x80000000u;
+static_assert(kSetupCellsPerThread == kGhostGroup, "one set-up thread scans one ghost group");
 
 // Error bits raised by setup_mask.
 constexpr uint32_t kErrPorosity = 1u;  // porosity outside (0, 1] on a non-solid cell

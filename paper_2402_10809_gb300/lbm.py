@@ -19,7 +19,7 @@ STORAGE = {"f32": LBM_F32, "f16dev": LBM_F16DEV, "bf16dev": LBM_BF16DEV}
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EUNSTABLE", 5: "LBM_ESTATE"}
 
 # Symbols include/lbm.h declares (checked by the tests).
-SYMBOLS = ["lbm_workspace_size", "lbm_init", "lbm_step", "lbm_moments", "lbm_diag", "lbm_diag_noalloc",
+SYMBOLS = ["lbm_list_length", "lbm_workspace_size", "lbm_init", "lbm_step", "lbm_moments", "lbm_diag", "lbm_diag_noalloc",
            "lbm_set_check",
            "lbm_state_size", "lbm_save", "lbm_load", "lbm_time", "lbm_fluid_count", "lbm_last_error",
            "lbm_destroy"]
@@ -72,6 +72,8 @@ def load(build_if_missing=True):
         raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build()")
     L = C.CDLL(path)
     P, vp = C.POINTER, C.c_void_p
+    L.lbm_list_length.restype = C.c_int64
+    L.lbm_list_length.argtypes = [P(lbm_grid), vp]
     L.lbm_workspace_size.restype = C.c_size_t
     L.lbm_workspace_size.argtypes = [P(lbm_grid), C.c_int64]
     L.lbm_init.restype = C.c_int
@@ -138,8 +140,12 @@ def make_params(rheology, porous, bc):
 
 # ----------------------------------------------------------------- C ABI, same names
 
-def lbm_workspace_size(grid, n_fluid=-1):
-    return int(load().lbm_workspace_size(C.byref(grid), int(n_fluid)))
+def lbm_list_length(grid, flags_host):
+    return int(load().lbm_list_length(C.byref(grid), C.c_void_p(flags_host)))
+
+
+def lbm_workspace_size(grid, n_list=-1):
+    return int(load().lbm_workspace_size(C.byref(grid), int(n_list)))
 
 
 def lbm_init(grid, flags, porosity, inputs_on_device, rheology, porous, bc, workspace, workspace_bytes, stream):
@@ -233,8 +239,8 @@ class Simulation:
         self.rheo, self.por, self.bc = make_params(problem.rheology, problem.porous, problem.bc)
         flags = np.ascontiguousarray(problem.flags, dtype=np.uint8)
         phi = np.ascontiguousarray(problem.phi, dtype=np.float32)
-        n_fluid = int(np.count_nonzero(flags))
-        nbytes = lbm_workspace_size(self.grid, n_fluid)
+        n_list = lbm_list_length(self.grid, flags.ctypes.data)
+        nbytes = lbm_workspace_size(self.grid, n_list)
         if nbytes == 0:
             raise LBMError(LBM_EINVAL, "bad grid")
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)

@@ -36,7 +36,13 @@ def test_workspace_size_host_logic():
 
     g = lbm.make_grid((32, 32, 64), 19, "f32", (0, 0, 1))
     full = lbm.lbm_workspace_size(g, -1)
-    tight = lbm.lbm_workspace_size(g, 39424)
+    from lbm_inputs import pipe_problem
+    import numpy as np
+
+    flags = np.ascontiguousarray(pipe_problem().flags)
+    n_list = lbm.lbm_list_length(g, flags.ctypes.data)
+    assert 39424 < n_list < 32 * 32 * 64  # fluid cells plus ghost entries
+    tight = lbm.lbm_workspace_size(g, n_list)
     assert full > tight > 2 * 19 * 32 * 32 * 64 * 4
     g16 = lbm.make_grid((32, 32, 64), 19, "f16dev", (0, 0, 1))
     assert lbm.lbm_workspace_size(g16, 39424) < tight

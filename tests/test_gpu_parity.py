@@ -209,7 +209,7 @@ def test_workspace_too_small(lbm):
     prob = pipe_problem()
     g = lbm.make_grid(prob.dims, 19, "f32", prob.periodic)
     r, p, b = lbm.make_params(prob.rheology, prob.porous, prob.bc)
-    need = lbm.lbm_workspace_size(g, prob.n_fluid)
+    need = lbm.lbm_workspace_size(g, lbm.lbm_list_length(g, np.ascontiguousarray(prob.flags).ctypes.data))
     ws = torch.empty(need - 4096, dtype=torch.uint8, device="cuda")
     flags = np.ascontiguousarray(prob.flags)
     phi = np.ascontiguousarray(prob.phi)
