@@ -167,6 +167,33 @@ lbm_status lbm_diag_noalloc(lbm_ctx* ctx, const uint8_t* region, double out[8]);
  * lbm_diag and return LBM_EUNSTABLE when it is nonzero (0 = never, default). */
 lbm_status lbm_set_check(lbm_ctx* ctx, int32_t check_every);
 
+/* Discrete adjoint (reverse mode of the time step of lbm_step) for gradients
+ * of a sac flow quantity with respect to the porosity field phi, the coil
+ * distribution of Sec. 2 (the paper itself runs forward simulations only; the
+ * objective below is its sac-averaged flow quantity of Sec. 4 made a scalar):
+ *     J = (1/T) sum_{t=1..T} (1/|R|) sum_{y in R} rho(t, y) |u(t, y)|^2 / 2,
+ * R = non-solid cells whose region byte is nonzero, rho and u as in the
+ * collision of time t.  The call restarts from the rest state of lbm_init
+ * (t = 0), runs T forward steps keeping a checkpoint every K steps, then sweeps
+ * backwards, replaying one segment of K steps at a time from its checkpoint.
+ * The context's own state and time are left untouched.
+ *
+ * lbm_adjoint_workspace_size: bytes of device workspace for (T, K); 0 on an
+ *   invalid context or T < 1 or K < 1.  About (ceil(T/K) + min(K, T)) states
+ *   in the storage type plus min(K, T) dense FP32 density fields plus two FP32
+ *   adjoint states.  K >= T keeps the whole trajectory (no replay).
+ * lbm_adjoint:
+ *   region   [N] uint8, host or device memory (region_on_device);
+ *   workspace / workspace_bytes: caller-owned device memory, 256-byte aligned;
+ *   grad     [N] FP64 device memory, overwritten with dJ/dphi (0 on solid
+ *            cells); the accumulation over time steps is in FP64;
+ *   J        host double, the objective value.
+ * Synchronises the context's stream.  LBM_EINVAL on bad arguments or a region
+ * without fluid cells, LBM_ENOMEM when the workspace is too small. */
+size_t lbm_adjoint_workspace_size(const lbm_ctx* ctx, int32_t T, int32_t K);
+lbm_status lbm_adjoint(lbm_ctx* ctx, int32_t T, int32_t K, const uint8_t* region, int32_t region_on_device,
+                       void* workspace, size_t workspace_bytes, double* grad, double* J);
+
 /* Checkpoint of the full state (distributions, relaxation rates, time): size in
  * bytes, save into / load from caller memory (host or device). */
 size_t lbm_state_size(const lbm_ctx* ctx);

@@ -22,6 +22,8 @@ UNITS = [("setup", "setup.cu", []), ("api", "api.cu", [])]
 for q in (19, 27):
     for s, name in ((0, "f32"), (1, "f16"), (2, "bf16")):
         UNITS.append((f"step_{q}_{name}", "step.cu", [f"-DLBM_Q={q}", f"-DLBM_STORE={s}", "--use_fast_math"]))
+        UNITS.append((f"adjoint_{q}_{name}", "adjoint.cu",
+                      [f"-DLBM_Q={q}", f"-DLBM_STORE={s}", "--use_fast_math"]))
 
 
 def _sources():

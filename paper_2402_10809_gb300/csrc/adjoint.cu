@@ -1,0 +1,46 @@
+// One translation unit per (velocity set, storage type), like step.cu: the
+// reverse time step and the outlet fix-up of the discrete adjoint.
+#include <cuda_runtime.h>
+
+#include "adjoint.cuh"
+
+#ifndef LBM_Q
+#error "LBM_Q must be defined"
+#endif
+#ifndef LBM_STORE
+#error "LBM_STORE must be defined"
+#endif
+
+#if LBM_STORE == 0
+#define LBM_T float
+#define LBM_TNAME f32
+#elif LBM_STORE == 1
+#define LBM_T __half
+#define LBM_TNAME f16
+#else
+#define LBM_T __nv_bfloat16
+#define LBM_TNAME bf16
+#endif
+
+#define LBM_CAT2(a, b, c) launch_adjoint_##a##_##b
+#define LBM_CAT(a, b) LBM_CAT2(a, b, 0)
+#define LBM_LAUNCHER LBM_CAT(LBM_Q, LBM_TNAME)
+
+namespace lbm {
+
+// what = 0: reverse time step; what = 1: outlet fix-up.
+cudaError_t LBM_LAUNCHER(int what, const AdjParams& A, cudaStream_t s)
+{
+    if (what == 0) {
+        const int grid = total_blocks(A.F);
+        if (grid == 0) return cudaSuccess;
+        adjoint_kernel<LBM_Q, LBM_T><<<grid, kBlock, 0, s>>>(A);
+    } else {
+        const int n = A.F.n_cells - A.F.n_bulk;
+        if (n == 0) return cudaSuccess;
+        adjoint_outlet_fixup<LBM_Q><<<(n + 127) / 128, 128, 0, s>>>(A);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

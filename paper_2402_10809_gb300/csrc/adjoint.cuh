@@ -1,0 +1,586 @@
+// Discrete adjoint of the fused VANSE LBM time step (reverse mode of the step
+// in kernels.cuh), for gradients of a sac objective with respect to the
+// porosity field phi (Sec. 2: phi is the coil's volume fraction complement,
+// the design variable of a coil distribution).
+//
+// Notation.  S(t) is the stored post-collision state of time t (deviation
+// form), omega(t) the relaxation rate of the collision of time t, f(t) the
+// pre-collision populations of time t (S(t-1) pulled, boundary conditions of
+// time t applied).  The objective is
+//     J = kappa sum_{t=1..T} sum_{y in R} rho(t, y) |u(t, y)|^2 / 2,
+// kappa = 1 / (T |R|), with rho and u from f(t) as in the collision of time t.
+// The adjoint states are lambda(t) = dJ/dS(t) (FP32, same [Q][N] layout) and
+// mu(t) = dJ/domega(t) (list order).
+//
+// The pull of step t reads every slot of S(t-1) exactly once (normal pull by
+// y + c_i, or the cell's own bounce-back), so its transpose is a permutation:
+// each cell writes the adjoints of its pulled values straight back to their
+// source slots, without atomics.  Two couplings reach other cells:
+//  * the porosity link term w_i (rho - 1)(phi(y + c_i) - phi(y)) of the
+//    collision at time t-1 gives dJ/dphi(y + c_i); the receiving cell gathers
+//    it while it writes lambda(t-1)[y, i], using rho(t-1) - 1 of the source cell;
+//  * the extrapolation outlet reads its interior neighbour's pulled values;
+//    its contributions go to a small per-outlet buffer that a fix-up kernel
+//    adds to the neighbour's source slots after the main kernel.
+// dJ/dphi accumulates in FP64 in a dense [N] array owned by the caller.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace lbm {
+
+struct AdjParams {
+    Params F;               // forward parameters: F.fsrc = S(t-1), F.omega = omega(t-1), F.t = t
+    const float* lam_in;    // lambda(t) [Q][N] (not read when first)
+    float* lam_out;         // lambda(t-1) [Q][N] (not written when last)
+    float* mu;              // [n_cells]: mu(t) in, mu(t-1) out
+    const float* drho_prev; // dense rho(t-1) - 1: porosity-link gather (not read when last)
+    double* gphi;           // dense dJ/dphi, accumulated
+    const uint8_t* region;  // dense objective region R
+    float kappa;            // 1 / (T |R|)
+    int first;              // t = T: no collision of time t in the objective's history
+    int objective;          // t >= 1: the kinetic-energy term of time t belongs to J
+    int last;               // t = 0: S(-1) and omega(-1) are constants
+    float* bnd_delta;       // [Q][n_cells - n_bulk]: outlet contributions to the neighbour's slots
+    double* bnd_dphi;       // [n_cells - n_bulk]: outlet contribution to the neighbour's porosity
+    double* jpart;          // [blocks]: per-block sums of the objective (accumulated over launches)
+};
+
+// ------------------------------------------------------------------ pieces
+
+// d alpha / d phi and d C1 / d phi of the coefficients of the explicit
+// velocity solve, alpha = K1 / (4 phi), C1 = K2 / (2 phi) (see darcy_coeffs).
+__device__ __forceinline__ void darcy_derivs(const Params& P, float phi, float iphi, float& dalpha, float& dc1)
+{
+    if (P.drag_kc) {
+        // alpha = A (1-phi)^2 / (4 phi^2), C1 = B (1-phi) / (2 phi)
+        const float s = 1.0f - phi;
+        dalpha = -0.5f * P.drag_a * s * iphi * iphi * iphi;
+        dc1 = -0.5f * P.drag_b * iphi * iphi;
+    } else if (phi < 1.0f) {
+        // alpha = A phi / 4, C1 = B sqrt(phi) / 2
+        dalpha = 0.25f * P.drag_a;
+        dc1 = 0.25f * P.drag_b * rsqrtf(phi);
+    } else {
+        dalpha = 0.0f;
+        dc1 = 0.0f;
+    }
+}
+
+// Reverse of macroscopic(): given the adjoints of its outputs (rho, rho - 1,
+// sigma, sd as used directly, u, F), adds the adjoints of its inputs: sd
+// (returned), the first moment m and phi.
+struct MacroBar {
+    float rho, drho, sigma, sd;
+    float ux, uy, uz, Fx, Fy, Fz;
+};
+
+__device__ __forceinline__ float macro_adjoint(const Params& P, float phi, float mx, float my, float mz,
+                                               const Macro& M, MacroBar b, float& mbx, float& mby, float& mbz,
+                                               float& phib)
+{
+    const float iphi = __frcp_rn(phi);
+    const float isig = __fdividef(1.0f, M.sigma);
+    const float hg = 0.5f * iphi;
+    const float vx = fmaf(P.gx, hg, mx * isig);
+    const float vy = fmaf(P.gy, hg, my * isig);
+    const float vz = fmaf(P.gz, hg, mz * isig);
+    float k1, k2;
+    darcy_coeffs(P, phi, iphi, k1, k2);
+    const float alpha = 0.25f * k1 * iphi;
+    const float c1 = 0.5f * k2 * iphi;
+    const float vn = sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
+    const float c1v = c1 * vn;
+    const float c0 = 0.5f + alpha;
+    const float r = sqrtf(fmaf(c0, c0, c1v));
+    const float dm1 = alpha + __fdividef(fmaf(alpha, alpha, alpha + c1v), r + 0.5f);
+    const float id = __fdividef(1.0f, 1.0f + dm1);
+    // F = rho g - 2 sigma (D - 1) u
+    b.rho += fmaf(b.Fx, P.gx, fmaf(b.Fy, P.gy, b.Fz * P.gz));
+    const float Fu = fmaf(b.Fx, M.ux, fmaf(b.Fy, M.uy, b.Fz * M.uz));
+    b.sigma -= 2.0f * dm1 * Fu;
+    float dm1b = -2.0f * M.sigma * Fu;
+    const float s2 = 2.0f * M.sigma * dm1;
+    b.ux -= s2 * b.Fx;
+    b.uy -= s2 * b.Fy;
+    b.uz -= s2 * b.Fz;
+    // u = v / D
+    float vbx = b.ux * id, vby = b.uy * id, vbz = b.uz * id;
+    dm1b -= fmaf(b.ux, M.ux, fmaf(b.uy, M.uy, b.uz * M.uz)) * id;
+    // D - 1 = c0 + sqrt(c0^2 + C1 |v|) - 1, c0 = 1/2 + alpha
+    const float ir = __fdividef(1.0f, r);
+    const float alphab = dm1b * fmaf(c0, ir, 1.0f);
+    const float c1vb = 0.5f * dm1b * ir;
+    const float c1b = c1vb * vn;
+    if (vn > 0.0f) {
+        const float k = c1vb * c1 * __fdividef(1.0f, vn);
+        vbx = fmaf(k, vx, vbx);
+        vby = fmaf(k, vy, vby);
+        vbz = fmaf(k, vz, vbz);
+    }
+    // v = m / sigma + g / (2 phi)
+    mbx = vbx * isig;
+    mby = vby * isig;
+    mbz = vbz * isig;
+    b.sigma -= fmaf(vbx, mx, fmaf(vby, my, vbz * mz)) * isig * isig;
+    phib -= 0.5f * fmaf(vbx, P.gx, fmaf(vby, P.gy, vbz * P.gz)) * iphi * iphi;
+    float dalpha, dc1;
+    darcy_derivs(P, phi, iphi, dalpha, dc1);
+    phib = fmaf(alphab, dalpha, fmaf(c1b, dc1, phib));
+    // in the independent variables (phi, sd): sigma = phi + sd and
+    // rho = 1 + sd / phi, so d rho / d phi = -(rho - 1) / phi (taking it as
+    // d(sigma/phi) would cancel two O(1) terms at rho ~ 1)
+    const float rd = (b.rho + b.drho) * iphi;
+    b.sd += b.sigma + rd;
+    phib += b.sigma - rd * M.drho;
+    return b.sd;
+}
+
+// Reverse of zou_he() in place on park (adjoints of the populations after the
+// boundary condition in, adjoints of the pulled populations out; the unknown
+// slots end at zero).  The condition is affine in the pulled populations and
+// in phi of the inlet cell: with P = phi rho = (g0 + 2 gm + phi) / (1 - ub.n),
+// unknown g_i = g_opp + 6 w_i P (c_i.ub) minus the tangential corrections
+// c_i,t N_t / n_t, N_t = sum_{c.n=0} (g_k - w_k (P - phi + P pe_k)) c_k,t.
+template <int Q>
+__device__ __forceinline__ void zou_he_adjoint(const Params& P, float prof, volatile float* park, float& phib)
+{
+    using L = Lattice<Q>;
+    const int ax = P.in_axis;
+    const int sgn = P.in_side == 0 ? 1 : -1;
+    const float un = (float)((double)prof * inflow_mean(P, P.t));
+    const float ubx = -0.5f * P.gx + (ax == 0 ? sgn * un : 0.0f);
+    const float uby = -0.5f * P.gy + (ax == 1 ? sgn * un : 0.0f);
+    const float ubz = -0.5f * P.gz + (ax == 2 ? sgn * un : 0.0f);
+    const float ubn = (ax == 0 ? ubx : ax == 1 ? uby : ubz) * sgn;
+    const float uu = ubx * ubx + uby * uby + ubz * ubz;
+    const float inv = 1.0f / (1.0f - ubn);
+    float Pb = 0.0f;
+#pragma unroll
+    for (int tg = 0; tg < 3; ++tg) {
+        if (tg == ax) continue;
+        float ncnt = 0.0f, nb = 0.0f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (c_axis<Q>(i, ax) * sgn > 0) {
+                const int ct = c_axis<Q>(i, tg);
+                ncnt += (float)(ct * ct);
+                if (ct) nb -= ct * park[i * kBlock];
+            }
+        }
+        nb /= ncnt;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int ct = c_axis<Q>(k, tg);
+            if (c_axis<Q>(k, ax) * sgn == 0 && ct != 0) {
+                const float cu = cdot(L::cx(k), L::cy(k), L::cz(k), ubx, uby, ubz);
+                const float pe = 3.0f * cu + 4.5f * cu * cu - 1.5f * uu;
+                park[k * kBlock] += nb * ct;
+                Pb -= nb * L::w(k) * (1.0f + pe) * ct;
+                phib += nb * L::w(k) * ct;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (c_axis<Q>(i, ax) * sgn > 0) {
+            const float a = park[i * kBlock];
+            const float cu = cdot(L::cx(i), L::cy(i), L::cz(i), ubx, uby, ubz);
+            park[opp(i) * kBlock] += a;
+            Pb += 6.0f * L::w(i) * cu * a;
+            park[i * kBlock] = 0.0f;
+        }
+    }
+    const float pw = Pb * inv;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const int cn = c_axis<Q>(k, ax) * sgn;
+        if (cn == 0) park[k * kBlock] += pw;
+        if (cn < 0) park[k * kBlock] += 2.0f * pw;
+    }
+    phib += pw;
+}
+
+// Reverse of outlet(): the unknown populations
+//   g_i = w_i phi (rho_out - 1) + w_i (phi rho_out - sigma_nb) pe_i(u_nb) + g_nb,i - w_i sd_nb
+// depend on this cell's phi and on the interior neighbour nb (its pulled
+// populations and phi).  The neighbour's part is stored for the fix-up kernel;
+// the unknown slots of this cell end at zero.
+template <int Q, class T>
+__device__ __forceinline__ void outlet_adjoint(const AdjParams& A, const Coords& c, float phi, int q,
+                                               volatile float* park, float& phib)
+{
+    using L = Lattice<Q>;
+    const Params& P = A.F;
+    const int ax = P.out_axis;
+    const int sgn = P.out_side == 1 ? -1 : 1;
+    const uint32_t nbmask = P.bnd_nbmask[q];
+    const Coords nc = make_coords(P, c.x + (ax == 0 ? sgn : 0), c.y + (ax == 1 ? sgn : 0), c.z + (ax == 2 ? sgn : 0));
+    const float phin = __ldg(P.phi + nc.idx);
+    const T* f = static_cast<const T*>(P.fsrc);
+    float sd = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float v = Store<T>::ld(f + pull_offset<Q>(P.N, nc, nbmask, i));
+        sd += v;
+        if (L::cx(i)) mx += L::cx(i) > 0 ? v : -v;
+        if (L::cy(i)) my += L::cy(i) > 0 ? v : -v;
+        if (L::cz(i)) mz += L::cz(i) > 0 ? v : -v;
+    }
+    const Macro M = macroscopic(P, phin, sd, mx, my, mz);
+    const float uu = M.ux * M.ux + M.uy * M.uy + M.uz * M.uz;
+    // phi rho_out - sigma_nb without cancelling O(1) terms
+    const float sfac = fmaf(phi, P.rho_out - 1.0f, (phi - phin) - M.sd);
+    MacroBar b{};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (c_axis<Q>(i, ax) * sgn > 0) {
+            const float d = park[i * kBlock];
+            const float w = L::w(i);
+            const float cu = cdot(L::cx(i), L::cy(i), L::cz(i), M.ux, M.uy, M.uz);
+            const float pe = 3.0f * cu + 4.5f * cu * cu - 1.5f * uu;
+            phib += d * w * (P.rho_out - 1.0f + P.rho_out * pe);
+            b.sigma -= d * w * pe;
+            b.sd -= d * w;
+            // d pe / d u = 3 c + 9 (c.u) c - 3 u
+            const float k = d * w * sfac;
+            const float kc = k * fmaf(9.0f, cu, 3.0f);
+            b.ux += (L::cx(i) ? (L::cx(i) > 0 ? kc : -kc) : 0.0f) - 3.0f * k * M.ux;
+            b.uy += (L::cy(i) ? (L::cy(i) > 0 ? kc : -kc) : 0.0f) - 3.0f * k * M.uy;
+            b.uz += (L::cz(i) ? (L::cz(i) > 0 ? kc : -kc) : 0.0f) - 3.0f * k * M.uz;
+        }
+    }
+    float mbx, mby, mbz, phinb = 0.0f;
+    const float sdb = macro_adjoint(P, phin, mx, my, mz, M, b, mbx, mby, mbz, phinb);
+    const int nb_count = P.n_cells - P.n_bulk;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        float d = sdb;
+        if (L::cx(j)) d += L::cx(j) > 0 ? mbx : -mbx;
+        if (L::cy(j)) d += L::cy(j) > 0 ? mby : -mby;
+        if (L::cz(j)) d += L::cz(j) > 0 ? mbz : -mbz;
+        if (c_axis<Q>(j, ax) * sgn > 0) {
+            d += park[j * kBlock];
+            park[j * kBlock] = 0.0f;
+        }
+        A.bnd_delta[(size_t)j * nb_count + q] = d;
+    }
+    A.bnd_dphi[q] = phinb;
+}
+
+// ------------------------------------------------------------------ the cell
+
+// Reverse of one cell of the time step t (see cell_impl): recompute the
+// forward quantities from S(t-1), omega(t-1), form the adjoints of the pulled
+// populations and write them to lambda(t-1) at the source slots; add the
+// cell's dJ/dphi terms; write mu(t-1).  jv accumulates the objective term.
+template <int Q, class T, bool fast>
+__device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t idx, uint32_t mask,
+                                             volatile float* park, double& jv)
+{
+    using L = Lattice<Q>;
+    const Params& P = A.F;
+    if (fast && (idx & 0x80000000u)) return;  // ghost entry: no state
+    const float phi = __ldg(P.phi + idx);
+    const T* __restrict__ fs = static_cast<const T*>(P.fsrc);
+    const uint32_t N = (uint32_t)P.N;
+    const int sy = P.nx, sz = P.nx * P.ny;
+    int type = kBulk;
+    Coords cg;
+    {
+        float g[Q];
+        if (fast) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const uint32_t d = (uint32_t)(L::cx(i) + L::cy(i) * sy + L::cz(i) * sz);
+                const uint32_t o = ((mask >> i) & 1u) ? (uint32_t)opp(i) * N + idx : (uint32_t)i * N + idx - d;
+                g[i] = Store<T>::ld(fs + o);
+            }
+        } else {
+            cg = coords_of(P, idx);
+            pull_general<Q, T>(fs, P.N, cg, mask, g);
+            type = (mask >> kTypeShift) & 3u;
+            if (type == kInlet) {
+                zou_he<Q>(P, P.bnd_prof[p - P.n_bulk], g);
+            } else if (type == kOutlet) {
+                outlet<Q, T>(P, cg, phi, P.bnd_nbmask[p - P.n_bulk], g);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) park[i * kBlock] = g[i];
+    }
+    // ---- forward recompute (as in cell_impl)
+    float smx, smy, smz;
+    Macro M;
+    float pxx, pyy, pzz, pxy, pxz, pyz;
+    {
+        float g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = park[i * kBlock];
+        const Moments<Q> m = moments<Q>(g);
+        smx = m.mx;
+        smy = m.my;
+        smz = m.mz;
+        M = macroscopic(P, phi, m.sd, m.mx, m.my, m.mz);
+        const float sd3 = M.sd * (1.0f / 3.0f);
+        pxx = fmaf(M.ux, fmaf(-M.sigma, M.ux, M.Fx), m.sxx - sd3);
+        pyy = fmaf(M.uy, fmaf(-M.sigma, M.uy, M.Fy), m.syy - sd3);
+        pzz = fmaf(M.uz, fmaf(-M.sigma, M.uz, M.Fz), m.szz - sd3);
+        pxy = fmaf(M.ux, fmaf(-M.sigma, M.uy, 0.5f * M.Fy), fmaf(0.5f * M.Fx, M.uy, m.sxy));
+        pxz = fmaf(M.ux, fmaf(-M.sigma, M.uz, 0.5f * M.Fz), fmaf(0.5f * M.Fx, M.uz, m.sxz));
+        pyz = fmaf(M.uy, fmaf(-M.sigma, M.uz, 0.5f * M.Fz), fmaf(0.5f * M.Fy, M.uz, m.syz));
+    }
+    const float pn = sqrtf(fmaf(pxx, pxx, fmaf(pyy, pyy, fmaf(pzz, pzz, 2.0f * fmaf(pxy, pxy, fmaf(pxz, pxz, pyz * pyz))))));
+    const float om_prev = P.omega[p];
+    const float irho = __fdividef(1.0f, M.rho);
+    const float gdot = 3.0f * om_prev * pn * irho;
+    // Carreau-Yasuda viscosity and rate with the pieces of their derivatives
+    const float x = P.lam * gdot;
+    const float xa = P.cy_a_two ? x * x : __powf(x, P.cy_a);
+    const float base = 1.0f + xa;
+    const float pw = exp2f(P.cy_e * __log2f(base));
+    const float mu = fmaf(P.mu0 - P.mu_inf, pw, P.mu_inf);
+    const float E = fmaf(6.0f, mu, M.rho);
+    const float iE = __fdividef(1.0f, E);
+    const float om = 2.0f * M.rho * iE;
+
+    // ---- reverse of the collision: out_i = (1 - omega) g_i
+    //      + w_i [omega (sd + sigma pe_i) + (1 - omega/2) q_i] + w_i (rho - 1)(phi_i - phi),
+    // pe_i = 3 c.u + 4.5 (c.u)^2 - 1.5 u.u, q_i = 3 c.F - 3 u.F + 9 (c.u)(c.F).
+    MacroBar b{};
+    float omb = 0.0f, phib = 0.0f;
+    if (!A.first) {
+        const float* __restrict__ la = A.lam_in + idx;
+        float h[Q];
+        float Ag = 0.0f, Wd = 0.0f, Aphi = 0.0f;
+        const bool porous = (mask & kPorousBit) != 0u;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float a = __ldcs(la + (size_t)i * N);
+            Ag = fmaf(a, park[i * kBlock], Ag);
+            park[i * kBlock] = a;
+            h[i] = L::w(i) * a;
+            // the link term exists where y + c_i (i != 0) is a fluid cell that
+            // pulls from y (mask bit of the opposite direction clear)
+            if (i != 0 && !((mask >> opp(i)) & 1u)) {
+                Wd += h[i];
+                if (porous) {
+                    uint32_t ni;
+                    if (fast)
+                        ni = idx + (uint32_t)(L::cx(i) + L::cy(i) * sy + L::cz(i) * sz);
+                    else
+                        ni = (uint32_t)shifted(cg, L::cx(i), L::cy(i), L::cz(i));
+                    Aphi = fmaf(h[i], __ldg(P.phi + ni) - phi, Aphi);
+                }
+            }
+        }
+        const Moments<Q> am = moments<Q>(h);  // A0, A1, A2 = sums of w a, w a c, w a c c
+        const float bmu = A.mu[p];
+        const float A0 = am.sd;
+        const float uu = fmaf(M.ux, M.ux, fmaf(M.uy, M.uy, M.uz * M.uz));
+        const float uF = fmaf(M.ux, M.Fx, fmaf(M.uy, M.Fy, M.uz * M.Fz));
+        // A2 u, A2 F
+        const float A2ux = fmaf(am.sxx, M.ux, fmaf(am.sxy, M.uy, am.sxz * M.uz));
+        const float A2uy = fmaf(am.sxy, M.ux, fmaf(am.syy, M.uy, am.syz * M.uz));
+        const float A2uz = fmaf(am.sxz, M.ux, fmaf(am.syz, M.uy, am.szz * M.uz));
+        const float A2Fx = fmaf(am.sxx, M.Fx, fmaf(am.sxy, M.Fy, am.sxz * M.Fz));
+        const float A2Fy = fmaf(am.sxy, M.Fx, fmaf(am.syy, M.Fy, am.syz * M.Fz));
+        const float A2Fz = fmaf(am.sxz, M.Fx, fmaf(am.syz, M.Fy, am.szz * M.Fz));
+        const float A1u = fmaf(am.mx, M.ux, fmaf(am.my, M.uy, am.mz * M.uz));
+        const float A1F = fmaf(am.mx, M.Fx, fmaf(am.my, M.Fy, am.mz * M.Fz));
+        const float uA2u = fmaf(A2ux, M.ux, fmaf(A2uy, M.uy, A2uz * M.uz));
+        const float uA2F = fmaf(A2Fx, M.ux, fmaf(A2Fy, M.uy, A2Fz * M.uz));
+        const float Ape = 3.0f * A1u + 4.5f * uA2u - 1.5f * uu * A0;
+        const float Aq = 3.0f * A1F - 3.0f * uF * A0 + 9.0f * uA2F;
+        const float h2 = fmaf(-0.5f, om, 1.0f);
+        omb = bmu - Ag + M.sd * A0 + M.sigma * Ape - 0.5f * Aq;
+        b.sd = om * A0;
+        b.sigma = om * Ape;
+        b.drho = Aphi;
+        // Bu = 3 A1 + 9 A2 u - 3 A0 u, BF = 9 A2 F - 3 A0 F
+        const float Bux = 3.0f * am.mx + 9.0f * A2ux - 3.0f * A0 * M.ux;
+        const float Buy = 3.0f * am.my + 9.0f * A2uy - 3.0f * A0 * M.uy;
+        const float Buz = 3.0f * am.mz + 9.0f * A2uz - 3.0f * A0 * M.uz;
+        const float os = om * M.sigma;
+        b.ux = os * Bux + h2 * (9.0f * A2Fx - 3.0f * A0 * M.Fx);
+        b.uy = os * Buy + h2 * (9.0f * A2Fy - 3.0f * A0 * M.Fy);
+        b.uz = os * Buz + h2 * (9.0f * A2Fz - 3.0f * A0 * M.Fz);
+        b.Fx = h2 * Bux;
+        b.Fy = h2 * Buy;
+        b.Fz = h2 * Buz;
+        phib = -M.drho * Wd;
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) park[i * kBlock] = 0.0f;
+    }
+    // omega = 2 rho / (6 mu + rho)
+    b.rho = omb * 12.0f * mu * iE * iE;
+    const float mub = -omb * 12.0f * M.rho * iE * iE;
+    // mu = mu_inf + (mu0 - mu_inf)(1 + x^a)^((n-1)/a):
+    // dmu/dx = (mu0 - mu_inf)(n - 1)(1 + x^a)^((n-1)/a - 1) x^(a-1)
+    const float xam1 = P.cy_a_two ? x : (x > 0.0f ? __fdividef(xa, x) : 0.0f);
+    const float dmudx = (P.mu0 - P.mu_inf) * (P.cy_e * P.cy_a) * __fdividef(pw, base) * xam1;
+    const float gdb = P.lam * mub * dmudx;
+    // gdot = 3 omega(t-1) |Pi| / rho
+    const float mu_prev = gdb * 3.0f * pn * irho;
+    const float pnb = gdb * 3.0f * om_prev * irho;
+    b.rho -= gdb * gdot * irho;
+    // objective term of time t
+    if (A.objective && A.region[idx]) {
+        const float uu = fmaf(M.ux, M.ux, fmaf(M.uy, M.uy, M.uz * M.uz));
+        jv += (double)A.kappa * 0.5 * (double)M.rho * (double)uu;
+        b.rho = fmaf(0.5f * A.kappa, uu, b.rho);
+        const float kr = A.kappa * M.rho;
+        b.ux = fmaf(kr, M.ux, b.ux);
+        b.uy = fmaf(kr, M.uy, b.uy);
+        b.uz = fmaf(kr, M.uz, b.uz);
+    }
+    // Pi = S - (sd/3) I - sigma u u^T + (F u^T + u F^T) / 2, |Pi| its Frobenius norm
+    const float s = pn > 0.0f ? __fdividef(pnb, pn) : 0.0f;
+    const float bxx = s * pxx, byy = s * pyy, bzz = s * pzz, bxy = s * pxy, bxz = s * pxz, byz = s * pyz;
+    {
+        const float Pux = fmaf(bxx, M.ux, fmaf(bxy, M.uy, bxz * M.uz));
+        const float Puy = fmaf(bxy, M.ux, fmaf(byy, M.uy, byz * M.uz));
+        const float Puz = fmaf(bxz, M.ux, fmaf(byz, M.uy, bzz * M.uz));
+        const float PFx = fmaf(bxx, M.Fx, fmaf(bxy, M.Fy, bxz * M.Fz));
+        const float PFy = fmaf(bxy, M.Fx, fmaf(byy, M.Fy, byz * M.Fz));
+        const float PFz = fmaf(bxz, M.Fx, fmaf(byz, M.Fy, bzz * M.Fz));
+        const float ts = -2.0f * M.sigma;
+        b.ux += fmaf(ts, Pux, PFx);
+        b.uy += fmaf(ts, Puy, PFy);
+        b.uz += fmaf(ts, Puz, PFz);
+        b.Fx += Pux;
+        b.Fy += Puy;
+        b.Fz += Puz;
+        b.sigma -= fmaf(Pux, M.ux, fmaf(Puy, M.uy, Puz * M.uz));
+        b.sd -= (bxx + byy + bzz) * (1.0f / 3.0f);
+    }
+    float mbx, mby, mbz;
+    const float sdb = macro_adjoint(P, phi, smx, smy, smz, M, b, mbx, mby, mbz, phib);
+
+    // ---- adjoints of the populations after the boundary condition:
+    // gbar_i = (1 - omega) a_i + sdbar + mbar.c_i + c_i^T Pibar c_i
+    const float omo = 1.0f - om;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        float v = fmaf(omo, park[i * kBlock], sdb);
+        if (cx) v += cx > 0 ? mbx : -mbx;
+        if (cy) v += cy > 0 ? mby : -mby;
+        if (cz) v += cz > 0 ? mbz : -mbz;
+        if (cx) v += bxx;
+        if (cy) v += byy;
+        if (cz) v += bzz;
+        if (cx && cy) v += cx * cy > 0 ? 2.0f * bxy : -2.0f * bxy;
+        if (cx && cz) v += cx * cz > 0 ? 2.0f * bxz : -2.0f * bxz;
+        if (cy && cz) v += cy * cz > 0 ? 2.0f * byz : -2.0f * byz;
+        park[i * kBlock] = v;
+    }
+    if (!fast) {
+        if (type == kInlet) {
+            zou_he_adjoint<Q>(P, P.bnd_prof[p - P.n_bulk], park, phib);
+        } else if (type == kOutlet) {
+            outlet_adjoint<Q, T>(A, cg, phi, p - P.n_bulk, park, phib);
+        }
+    }
+
+    // ---- transpose of the pull: lambda(t-1) at the source slots, plus the
+    // porosity-link gather w_i (rho(t-1, y - c_i) - 1) lambda(t-1)[y - c_i, i]
+    double gacc = (double)phib;
+    if (!A.last) {
+        float* __restrict__ lo = A.lam_out;
+        float gat = 0.0f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float v = park[i * kBlock];
+            const bool bb = ((mask >> i) & 1u) != 0u;
+            if (fast) {
+                const uint32_t d = (uint32_t)(L::cx(i) + L::cy(i) * sy + L::cz(i) * sz);
+                lo[bb ? (uint32_t)opp(i) * N + idx : (uint32_t)i * N + idx - d] = v;
+                if (!bb && i != 0) gat = fmaf(L::w(i) * __ldg(A.drho_prev + (idx - d)), v, gat);
+            } else {
+                lo[pull_offset<Q>(P.N, cg, mask, i)] = v;
+                if (!bb && i != 0)
+                    gat = fmaf(L::w(i) * __ldg(A.drho_prev + shifted(cg, -L::cx(i), -L::cy(i), -L::cz(i))), v, gat);
+            }
+        }
+        gacc += (double)gat;
+        A.mu[p] = mu_prev;
+    }
+    A.gphi[idx] += gacc;
+}
+
+template <int Q, class T>
+__device__ __noinline__ void adjoint_general(const AdjParams& A, int p, uint32_t idx, uint32_t mask,
+                                             volatile float* park, double& jv)
+{
+    adjoint_cell<Q, T, false>(A, p, idx, mask, park, jv);
+}
+
+template <int Q, class T>
+__global__ void __launch_bounds__(kBlock, 2) adjoint_kernel(const AdjParams A)
+{
+    const Params& P = A.F;
+    const int nbg = general_blocks(P);
+    const bool fast = (int)blockIdx.x >= nbg;
+    const int p = fast ? ((int)blockIdx.x - nbg) * kBlock + (int)threadIdx.x
+                       : P.n_fast + (int)blockIdx.x * kBlock + (int)threadIdx.x;
+    const int pend = fast ? P.n_fast : P.n_cells;
+    __shared__ float sg[Q * kBlock];
+    volatile float* park = sg + threadIdx.x;
+    double jv = 0.0;
+    if (p < pend) {
+        if (fast)
+            adjoint_cell<Q, T, true>(A, p, P.cells[p], P.mask[p], park, jv);
+        else
+            adjoint_general<Q, T>(A, p, P.cells[p], P.mask[p], park, jv);
+    }
+    if (A.objective) {
+        // block sum of the objective terms, added to this block's running partial
+        __shared__ double red[kBlock / 32];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) jv += __shfl_xor_sync(0xffffffffu, jv, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = jv;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < kBlock / 32; ++w) s += red[w];
+            A.jpart[blockIdx.x] += s;
+        }
+    }
+}
+
+// Fix-up after adjoint_kernel: adds each outlet's contributions to its interior
+// neighbour's source slots of lambda(t-1) (with the porosity-link gather those
+// slots carry) and to the neighbour's porosity.  One thread per boundary entry.
+template <int Q>
+__global__ void adjoint_outlet_fixup(const AdjParams A)
+{
+    using L = Lattice<Q>;
+    const Params& P = A.F;
+    const int nbc = P.n_cells - P.n_bulk;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nbc) return;
+    const int p = P.n_bulk + q;
+    if ((((uint32_t)P.mask[p] >> kTypeShift) & 3u) != kOutlet) return;
+    const Coords c = coords_of(P, P.cells[p]);
+    const int ax = P.out_axis;
+    const int sgn = P.out_side == 1 ? -1 : 1;
+    const Coords nc = make_coords(P, c.x + (ax == 0 ? sgn : 0), c.y + (ax == 1 ? sgn : 0), c.z + (ax == 2 ? sgn : 0));
+    const uint32_t nbmask = P.bnd_nbmask[q];
+    double acc = A.bnd_dphi[q];
+    if (!A.last) {
+        float gat = 0.0f;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const float d = A.bnd_delta[(size_t)j * nbc + q];
+            A.lam_out[pull_offset<Q>(P.N, nc, nbmask, j)] += d;
+            if (j != 0 && !((nbmask >> j) & 1u))
+                gat = fmaf(L::w(j) * A.drho_prev[shifted(nc, -L::cx(j), -L::cy(j), -L::cz(j))], d, gat);
+        }
+        acc += (double)gat;
+    }
+    A.gphi[nc.idx] += acc;
+}
+
+}  // namespace lbm

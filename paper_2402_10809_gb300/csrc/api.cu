@@ -11,7 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "kernels.cuh"
+#include "adjoint.cuh"
 #include "lbm.h"
 #include "setup.cuh"
 
@@ -22,6 +22,12 @@ cudaError_t launch_step_19_bf16(int, const Params&, cudaStream_t);
 cudaError_t launch_step_27_f32(int, const Params&, cudaStream_t);
 cudaError_t launch_step_27_f16(int, const Params&, cudaStream_t);
 cudaError_t launch_step_27_bf16(int, const Params&, cudaStream_t);
+cudaError_t launch_adjoint_19_f32(int, const AdjParams&, cudaStream_t);
+cudaError_t launch_adjoint_19_f16(int, const AdjParams&, cudaStream_t);
+cudaError_t launch_adjoint_19_bf16(int, const AdjParams&, cudaStream_t);
+cudaError_t launch_adjoint_27_f32(int, const AdjParams&, cudaStream_t);
+cudaError_t launch_adjoint_27_f16(int, const AdjParams&, cudaStream_t);
+cudaError_t launch_adjoint_27_bf16(int, const AdjParams&, cudaStream_t);
 }  // namespace lbm
 
 using namespace lbm;
@@ -553,6 +559,218 @@ extern "C" int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 extern "C" int64_t lbm_fluid_count(const lbm_ctx* c) { return c ? c->n_cells - c->n_ghost : -1; }
 extern "C" const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
 extern "C" void lbm_destroy(lbm_ctx* c) { delete c; }
+
+// ---------------------------------------------------------------------------
+// Discrete adjoint: d J / d phi of the sac kinetic-energy objective by a
+// checkpointed reverse sweep (kernels in adjoint.cuh).
+//
+// Pass 1 runs the T forward steps from the rest state and keeps the state
+// S(kK-1), omega(kK-1) and rho(kK-1) - 1 at the start of every segment k of K
+// steps; the last segment writes all its states straight into the history
+// slots.  The reverse sweep then visits the segments from last to first:
+// it replays a segment from its checkpoint into the history slots (states,
+// omega and the dense density deviation of every step), and runs the reverse steps
+// t = e-1 .. s of the segment (after the objective-only step t = T for the
+// last one).  Nothing is copied apart from the small omega arrays; every
+// state buffer is written in place by the step kernel.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct AdjLayout {
+    int nseg = 0, Kh = 0;  // segments; history slots H[1..Kh]
+    size_t sbytes = 0, wbytes = 0, rbytes = 0, lbytes = 0;
+    size_t ck = 0, hist = 0, wck = 0, whist = 0, rck = 0, rhist = 0, lam[2] = {0, 0};
+    size_t mu = 0, region = 0, jpart = 0, bdelta = 0, bdphi = 0, count = 0, end = 0;
+};
+
+AdjLayout adj_layout(const lbm_ctx* c, int T, int K)
+{
+    AdjLayout A;
+    A.nseg = (T + K - 1) / K;
+    A.Kh = K < T ? K : T;
+    const size_t N = (size_t)c->N, Q = (size_t)c->grid.q;
+    const size_t n = (size_t)(c->n_cells > 0 ? c->n_cells : 1);
+    const size_t nb = (size_t)(c->n_cells - c->n_bulk > 0 ? c->n_cells - c->n_bulk : 1);
+    A.sbytes = align256(Q * N * elem_size(c->grid.storage));
+    A.wbytes = align256(n * 4);
+    A.rbytes = align256(N * 4);
+    A.lbytes = align256(Q * N * 4);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    A.ck = take((size_t)A.nseg * A.sbytes);
+    A.hist = take((size_t)A.Kh * A.sbytes);
+    A.wck = take((size_t)A.nseg * A.wbytes);
+    A.whist = take((size_t)A.Kh * A.wbytes);
+    A.rck = take((size_t)A.nseg * A.rbytes);
+    A.rhist = take((size_t)A.Kh * A.rbytes);
+    A.lam[0] = take(A.lbytes);
+    A.lam[1] = take(A.lbytes);
+    A.mu = take(n * 4);
+    A.region = take(N);
+    A.jpart = take((size_t)(total_blocks(c->base) + 1) * 8);
+    A.bdelta = take(Q * nb * 4);
+    A.bdphi = take(nb * 8);
+    A.count = take(8);
+    A.end = o;
+    return A;
+}
+
+cudaError_t launch_adj(const lbm_grid& g, int what, const AdjParams& A, cudaStream_t s)
+{
+    if (g.q == 19) {
+        if (g.storage == LBM_F32) return launch_adjoint_19_f32(what, A, s);
+        if (g.storage == LBM_F16DEV) return launch_adjoint_19_f16(what, A, s);
+        return launch_adjoint_19_bf16(what, A, s);
+    }
+    if (g.storage == LBM_F32) return launch_adjoint_27_f32(what, A, s);
+    if (g.storage == LBM_F16DEV) return launch_adjoint_27_f16(what, A, s);
+    return launch_adjoint_27_bf16(what, A, s);
+}
+
+}  // namespace
+
+extern "C" size_t lbm_adjoint_workspace_size(const lbm_ctx* c, int32_t T, int32_t K)
+{
+    if (!c || !c->ready || T < 1 || K < 1) return 0;
+    return adj_layout(c, T, K).end;
+}
+
+extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, const uint8_t* region, int32_t region_on_device,
+                                  void* workspace, size_t workspace_bytes, double* grad, double* J)
+{
+    if (!c) return LBM_EINVAL;
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    if (T < 1 || K < 1) return fail(c, LBM_EINVAL, "T and K must be >= 1");
+    if (!region || !workspace || !grad || !J) return fail(c, LBM_EINVAL, "null pointer argument");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+        return fail(c, LBM_EINVAL, "adjoint workspace not 256-byte aligned");
+    const AdjLayout AL = adj_layout(c, T, K);
+    if (workspace_bytes < AL.end) return fail(c, LBM_ENOMEM, "workspace smaller than lbm_adjoint_workspace_size");
+    char* w = static_cast<char*>(workspace);
+    const cudaStream_t st = c->stream;
+    const size_t N = (size_t)c->N;
+    const size_t n = (size_t)c->n_cells;
+    auto Cs = [&](int k) { return static_cast<void*>(w + AL.ck + (size_t)k * AL.sbytes); };
+    auto Hs = [&](int j) { return static_cast<void*>(w + AL.hist + (size_t)(j - 1) * AL.sbytes); };
+    auto Wc = [&](int k) { return reinterpret_cast<float*>(w + AL.wck + (size_t)k * AL.wbytes); };
+    auto Wh = [&](int j) { return reinterpret_cast<float*>(w + AL.whist + (size_t)(j - 1) * AL.wbytes); };
+    auto Rc = [&](int k) { return reinterpret_cast<float*>(w + AL.rck + (size_t)k * AL.rbytes); };
+    auto Rh = [&](int j) { return reinterpret_cast<float*>(w + AL.rhist + (size_t)(j - 1) * AL.rbytes); };
+    float* lam[2] = {reinterpret_cast<float*>(w + AL.lam[0]), reinterpret_cast<float*>(w + AL.lam[1])};
+    float* mu = reinterpret_cast<float*>(w + AL.mu);
+    uint8_t* reg = reinterpret_cast<uint8_t*>(w + AL.region);
+    double* jpart = reinterpret_cast<double*>(w + AL.jpart);
+    const uint32_t* cells = c->base.cells;
+
+    LBM_CUDA(cudaMemcpyAsync(reg, region, N, region_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
+             "copy region");
+    unsigned long long* cnt_dev = reinterpret_cast<unsigned long long*>(w + AL.count);
+    unsigned long long cnt = 0;
+    LBM_CUDA(launch_region_count(cells, c->n_cells, reg, cnt_dev, st), "region count");
+    LBM_CUDA(cudaMemcpyAsync(&cnt, cnt_dev, sizeof(cnt), cudaMemcpyDeviceToHost, st), "copy region count");
+    LBM_CUDA(cudaStreamSynchronize(st), "region count sync");
+    if (cnt == 0) return fail(c, LBM_EINVAL, "the objective region holds no fluid cell");
+    const int nblk = total_blocks(c->base);
+    LBM_CUDA(cudaMemsetAsync(grad, 0, N * 8, st), "clear gradient");
+    LBM_CUDA(cudaMemsetAsync(Cs(0), 0, AL.sbytes, st), "rest state");
+    LBM_CUDA(cudaMemsetAsync(jpart, 0, (size_t)(nblk + 1) * 8, st), "clear objective partials");
+    LBM_CUDA(launch_fill_f32(Wc(0), (long long)n, c->omega0, st), "initial omega");
+
+    const Params B = c->base;
+    auto step = [&](long long t, const void* src, void* dst, float* om, float* rho) {
+        Params P = B;
+        P.fsrc = src;
+        P.fdst = dst;
+        P.omega = om;
+        P.o_drho = rho;
+        P.t = t;
+        return launch(c->grid, kModeStep, P, st);
+    };
+    auto copy_omega = [&](float* dst, const float* src) {
+        return n ? cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDeviceToDevice, st) : cudaSuccess;
+    };
+
+    // pass 1: forward with checkpoints
+    const int nseg = AL.nseg, kl = nseg - 1;
+    const void* src = Cs(0);
+    float* wcur = Wc(0);
+    for (int t = 0; t < T; ++t) {
+        const int k = t / K;
+        void* dst;
+        float* wdst;
+        float* rdst = nullptr;
+        if (k + 1 < nseg && t == (k + 1) * K - 1) {
+            dst = Cs(k + 1);
+            wdst = Wc(k + 1);
+            rdst = Rc(k + 1);
+        } else if (k == kl) {
+            const int j = t - k * K + 1;
+            dst = Hs(j);
+            wdst = Wh(j);
+            rdst = Rh(j);
+        } else {
+            dst = lam[t & 1];
+            wdst = mu;
+        }
+        if (wdst != wcur) LBM_CUDA(copy_omega(wdst, wcur), "omega copy");
+        LBM_CUDA(step(t, src, dst, wdst, rdst), "adjoint forward step");
+        src = dst;
+        wcur = wdst;
+    }
+
+    // reverse sweep
+    AdjParams A{};
+    A.F = B;
+    A.mu = mu;
+    A.gphi = grad;
+    A.region = reg;
+    A.kappa = (float)(1.0 / ((double)T * (double)cnt));
+    A.bnd_delta = reinterpret_cast<float*>(w + AL.bdelta);
+    A.bnd_dphi = reinterpret_cast<double*>(w + AL.bdphi);
+    A.jpart = jpart;
+    int li = 0;  // lam[li] holds lambda(t), lam[1 - li] receives lambda(t-1)
+    for (int k = kl; k >= 0; --k) {
+        const int s = k * K;
+        const int e = s + K < T ? s + K : T;
+        auto Sat = [&](int j) { return j == 0 ? Cs(k) : Hs(j); };
+        auto Wat = [&](int j) { return j == 0 ? Wc(k) : Wh(j); };
+        auto Rat = [&](int j) { return j == 0 ? Rc(k) : Rh(j); };
+        if (k < kl) {
+            // replay: S(t), omega(t), rho(t) - 1 for t = s .. e-2 (S(e-1) is the next checkpoint)
+            for (int t = s; t <= e - 2; ++t) {
+                const int j = t - s + 1;
+                LBM_CUDA(copy_omega(Wh(j), Wat(j - 1)), "omega copy");
+                LBM_CUDA(step(t, Sat(j - 1), Hs(j), Wh(j), Rh(j)), "adjoint replay step");
+            }
+        }
+        auto reverse = [&](int t, int first) {
+            const int j = t - s;
+            A.F.fsrc = Sat(j);
+            A.F.omega = Wat(j);
+            A.F.t = t;
+            A.drho_prev = Rat(j);
+            A.lam_in = lam[li];
+            A.lam_out = lam[1 - li];
+            A.first = first;
+            A.objective = t >= 1;
+            A.last = t == 0;
+            cudaError_t e1 = launch_adj(c->grid, 0, A, st);
+            if (e1 == cudaSuccess && c->n_out > 0) e1 = launch_adj(c->grid, 1, A, st);
+            li = 1 - li;
+            return e1;
+        };
+        if (k == kl) LBM_CUDA(reverse(T, 1), "adjoint objective step");
+        for (int t = e - 1; t >= s; --t) LBM_CUDA(reverse(t, 0), "adjoint reverse step");
+    }
+    std::vector<double> hp((size_t)nblk + 1, 0.0);
+    if (nblk > 0)
+        LBM_CUDA(cudaMemcpyAsync(hp.data(), jpart, (size_t)nblk * 8, cudaMemcpyDeviceToHost, st), "copy objective");
+    LBM_CUDA(cudaStreamSynchronize(st), "adjoint sync");
+    double sum = 0.0;
+    for (int b = 0; b < nblk; ++b) sum += hp[b];
+    *J = sum;
+    return LBM_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Diagnostics without any caller-provided scratch.

@@ -70,6 +70,7 @@ struct Params {
     // moments outputs (dense or list order, any may be null)
     float *o_rho, *o_ux, *o_uy, *o_uz, *o_gdot, *o_omega;
     int o_compact;
+    float* o_drho;            // time step: rho - 1 of time t (dense, may be null)
     // diagnostics
     const uint8_t* region;    // dense, may be null
     double* partials;         // [gridDim.x][kDiagSlots]
@@ -569,6 +570,7 @@ __device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t idx, 
             Store<T>::st(dp + (size_t)j * P.N, vj);
         }
         P.omega[p] = om;
+        if (P.o_drho) P.o_drho[idx] = M.drho;  // density deviation of time t (adjoint replay)
     } else if (MODE == kModeMoments) {
         const long long o = P.o_compact ? (long long)p : (long long)idx;
         if (P.o_rho) P.o_rho[o] = M.rho;

@@ -347,7 +347,43 @@ __global__ void diag_finish(const double* __restrict__ partials, int nblk, doubl
     }
 }
 
+// v into p[0..n).
+__global__ void fill_f32(float* p, long long n, float v)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// Number of listed non-ghost cells whose region byte is set.
+__global__ void region_count(const uint32_t* cells, int n_cells, const uint8_t* region, unsigned long long* out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    int hit = 0;
+    if (p < n_cells) {
+        const uint32_t e = cells[p];
+        hit = !(e & kGhostFlag) && region[e] ? 1 : 0;
+    }
+    const unsigned int warp_hits = __popc(__ballot_sync(0xffffffffu, hit));
+    if ((threadIdx.x & 31) == 0 && warp_hits) atomicAdd(out, (unsigned long long)warp_hits);
+}
+
 // Host launchers (kernel templates cannot be launched across translation units).
+cudaError_t launch_fill_f32(float* p, long long n, float v, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    fill_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_region_count(const uint32_t* cells, int n_cells, const uint8_t* region, unsigned long long* out,
+                                cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n_cells == 0) return e;
+    region_count<<<(n_cells + 255) / 256, 256, 0, s>>>(cells, n_cells, region, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_setup_mask(int q, const SetupParams& S, cudaStream_t s)
 {
     if (S.n_cells == 0) return cudaSuccess;

@@ -59,5 +59,8 @@ cudaError_t launch_init_state(int storage, const uint32_t* cells, int n_cells, i
 cudaError_t launch_pack_state(int storage, const uint32_t* cells, int n_cells, int nx, int ny, long long N, int Q,
                               void* f, void* state, int unpack, cudaStream_t s);
 cudaError_t launch_diag_finish(const double* partials, int nblk, double* out, cudaStream_t s);
+cudaError_t launch_fill_f32(float* p, long long n, float v, cudaStream_t s);
+cudaError_t launch_region_count(const uint32_t* cells, int n_cells, const uint8_t* region, unsigned long long* out,
+                                cudaStream_t s);
 
 }  // namespace lbm

@@ -22,7 +22,7 @@ STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM
 SYMBOLS = ["lbm_list_length", "lbm_workspace_size", "lbm_init", "lbm_step", "lbm_moments", "lbm_diag", "lbm_diag_noalloc",
            "lbm_set_check",
            "lbm_state_size", "lbm_save", "lbm_load", "lbm_time", "lbm_fluid_count", "lbm_last_error",
-           "lbm_destroy"]
+           "lbm_destroy", "lbm_adjoint_workspace_size", "lbm_adjoint"]
 
 
 class lbm_grid(C.Structure):
@@ -101,6 +101,10 @@ def load(build_if_missing=True):
     L.lbm_fluid_count.argtypes = [vp]
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_last_error.argtypes = [vp]
+    L.lbm_adjoint_workspace_size.restype = C.c_size_t
+    L.lbm_adjoint_workspace_size.argtypes = [vp, C.c_int32, C.c_int32]
+    L.lbm_adjoint.restype = C.c_int
+    L.lbm_adjoint.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, C.c_size_t, vp, P(C.c_double)]
     L.lbm_destroy.restype = None
     L.lbm_destroy.argtypes = [vp]
     _lib = L
@@ -218,6 +222,20 @@ def lbm_destroy(ctx):
     load().lbm_destroy(ctx)
 
 
+def lbm_adjoint_workspace_size(ctx, T, K):
+    return int(load().lbm_adjoint_workspace_size(ctx, int(T), int(K)))
+
+
+def lbm_adjoint(ctx, T, K, region, region_on_device, workspace, workspace_bytes, grad):
+    """Runs the adjoint; grad is the device address of an FP64 [N] array.
+    Returns J."""
+    J = C.c_double(0.0)
+    _check(ctx, load().lbm_adjoint(ctx, int(T), int(K), C.c_void_p(region), int(region_on_device),
+                                   C.c_void_p(workspace), C.c_size_t(workspace_bytes), C.c_void_p(grad),
+                                   C.byref(J)))
+    return float(J.value)
+
+
 # ----------------------------------------------------------------- convenience owner
 
 class Simulation:
@@ -312,3 +330,58 @@ class Simulation:
     def load_state(self, buf):
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         lbm_load(self.ctx, buf.ctypes.data, buf.size, 0)
+
+    def adjoint(self, T, K, region):
+        """(J, dJ/dphi) of the sac kinetic-energy objective over steps 1..T
+        with a checkpoint every K steps; dJ/dphi is an FP64 device tensor
+        shaped like the box."""
+        torch = self.torch
+        nbytes = lbm_adjoint_workspace_size(self.ctx, T, K)
+        if nbytes == 0:
+            raise LBMError(LBM_EINVAL, "T and K must be >= 1")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        grad = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        if hasattr(region, "data_ptr"):
+            reg = region.to(device=self.device, dtype=torch.uint8).contiguous()
+            J = lbm_adjoint(self.ctx, T, K, reg.data_ptr(), 1, ws.data_ptr(), nbytes, grad.data_ptr())
+        else:
+            reg = np.ascontiguousarray(region, dtype=np.uint8)
+            J = lbm_adjoint(self.ctx, T, K, reg.ctypes.data, 0, ws.data_ptr(), nbytes, grad.data_ptr())
+        return J, grad
+
+
+def sac_kinetic_energy(problem, phi, T, K, region, storage="f32"):
+    """J(phi) = time-and-sac mean of rho |u|^2 / 2 over steps 1..T, as a
+    differentiable torch function of the porosity tensor phi (any device; the
+    computation runs on the current CUDA device).  Backward returns the
+    gradient from the hand-written adjoint (lbm_adjoint)."""
+    import torch
+
+    class _SacKE(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, phi_t):
+            prob = _with_porosity(problem, phi_t.detach().cpu().numpy())
+            sim = Simulation(prob, storage=storage)
+            try:
+                J, grad = sim.adjoint(T, K, region)
+            finally:
+                sim.close()
+            ctx.save_for_backward(grad.to(device=phi_t.device, dtype=phi_t.dtype))
+            return torch.tensor(J, dtype=phi_t.dtype, device=phi_t.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (grad,) = ctx.saved_tensors
+            return gout * grad
+
+    return _SacKE.apply(phi)
+
+
+def _with_porosity(problem, phi):
+    import dataclasses
+
+    phi = np.ascontiguousarray(phi, dtype=np.float32)
+    if dataclasses.is_dataclass(problem):
+        return dataclasses.replace(problem, phi=phi)
+    problem.phi = phi
+    return problem
