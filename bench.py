@@ -62,7 +62,7 @@ def load_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def load_traffic(storage):
+def load_traffic(name, storage):
     """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
     only if it was taken on the current kernel sources."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -72,7 +72,7 @@ def load_traffic(storage):
         d = json.load(fh)
     if d.get("kernel_hash") != kernel_source_hash():
         return None
-    v = d.get("per_launch_bytes", {}).get(f"{WORKLOAD['name']}_{storage}")
+    v = d.get("per_launch_bytes", {}).get(f"{name}_{storage}")
     return v
 
 
@@ -174,14 +174,17 @@ def run_ours(args):
     from paper_2402_10809_gb300 import lbm
 
     lbm.load()
-    prob = aneurysm_problem(WORKLOAD["n"], q=WORKLOAD["q"], seed=WORKLOAD["seed"])
+    n = args.n
+    name = f"aneurysm{n}"
+    prob = aneurysm_problem(n, q=WORKLOAD["q"], seed=WORKLOAD["seed"])
     nf = prob.n_fluid
     L = args.lbm_steps
+    st0 = args.storage
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     peak, peak_kind = load_peaks()
 
     # ---- timed region: FP32 storage (the headline), barrier + sync on both sides
-    sim, _ = time_variant(torch, lbm, prob, "f32", 0, args.warmup, L, flush)
+    sim, _ = time_variant(torch, lbm, prob, st0, 0, args.warmup, L, flush)
     for _ in range(args.warmup):
         flush_l2(torch, flush)
         sim.step(L)
@@ -211,19 +214,19 @@ def run_ours(args):
     clocks = clk.summary()
     launch_s = total / (args.steps * L)  # average step-kernel launch duration (back-to-back launches)
     mlups = ws * nf * L * args.steps / total / 1e6
-    bpu = bytes_per_update(WORKLOAD["q"], "f32")
+    bpu = bytes_per_update(WORKLOAD["q"], st0)
     achieved = bpu * nf / launch_s / 1e9
-    traffic = load_traffic("f32")
+    traffic = load_traffic(name, st0)
 
     # ---- storage variants, same protocol
     variants = {}
-    for st in ("f16dev", "bf16dev"):
+    for st in () if args.no_variants else [v for v in ("f32", "f16dev", "bf16dev") if v != st0]:
         s2, tv = time_variant(torch, lbm, prob, st, max(3, args.steps // 2), args.warmup, L, flush)
         tv_mean = sum(tv) / len(tv)
         b2 = bytes_per_update(WORKLOAD["q"], st)
         variants[st] = {"value": nf * L / tv_mean / 1e6, "unit": UNIT,
                         "roofline_frac": b2 * nf / (tv_mean / L) / 1e9 / peak,
-                        "bytes_per_update": b2, "traffic": load_traffic(st)}
+                        "bytes_per_update": b2, "traffic": load_traffic(name, st)}
         s2.close()
 
     # ---- end to end through the C ABI with host buffers (pinned), per step:
@@ -233,7 +236,7 @@ def run_ours(args):
         pin_flags = torch.from_numpy(np.ascontiguousarray(prob.flags)).pin_memory()
         pin_phi = torch.from_numpy(np.ascontiguousarray(prob.phi)).pin_memory()
         pin_reg = torch.from_numpy(np.ascontiguousarray(prob.region)).pin_memory()
-        grid = lbm.make_grid(prob.dims, prob.q, "f32", prob.periodic)
+        grid = lbm.make_grid(prob.dims, prob.q, st0, prob.periodic)
         r, p, b = lbm.make_params(prob.rheology, prob.porous, prob.bc)
         nbytes = lbm.lbm_workspace_size(grid, lbm.lbm_list_length(grid, pin_flags.data_ptr()))
         wsb = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
@@ -264,22 +267,24 @@ def run_ours(args):
         "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD['name']} D3Q27 FP32-stored, {L} time steps per step, "
+        "config": {"workload": f"{name} D3Q27 {st0}-stored, {L} time steps per step, "
                                f"{nf} fluid cells, Carreau-Yasuda, porous sac, pulsatile inlet",
-                   "box": [WORKLOAD["n"]] * 3, "fluid_cells": nf, "time_steps_per_step": L,
-                   "q": WORKLOAD["q"], "storage": "f32", "parallelism": f"replicas{ws}",
-                   "l2": "inputs larger than L2 (412 MB touched per time step) and a 256 MB L2 flush "
+                   "box": [n] * 3, "fluid_cells": nf, "time_steps_per_step": L,
+                   "q": WORKLOAD["q"], "storage": st0, "parallelism": f"replicas{ws}",
+                   "l2": f"{bpu * nf / 1e6:.0f} MB touched per time step and a 256 MB L2 flush "
                          "before each timed step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "bytes_per_update": bpu,
-                     "kernel": "lbm_kernel<27,float,step> average over back-to-back launches"},
+                     "kernel": f"lbm_kernel<27,{st0},step> average over back-to-back launches"},
         "storage_variants": variants,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": args.steps * L,
     }
+    if rank == 0 and not args.no_adjoint:
+        line["adjoint"] = adjoint_cost(torch, lbm, args)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(prob, sim_factory=lambda st: lbm.Simulation(prob, storage=st),
                                             sample_steps=args.cpu_sample_steps)
@@ -289,6 +294,61 @@ def run_ours(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+ADJOINT = dict(name="aneurysm128", n=128, q=27, T=500, K=50, seed=0)
+
+
+def adjoint_cost(torch, lbm, args):
+    """Cost of lbm_adjoint (forward with checkpoints, segment replays, reverse
+    sweep) on the 128^3 aneurysm, T = 500 steps, checkpoint every K = 50 steps,
+    against T forward steps of the same problem; both timed with CUDA events on
+    the launching stream.  A second figure keeps the whole trajectory (K = T,
+    no replay) when the device has room for it."""
+    from lbm_inputs import aneurysm_problem
+
+    prob = aneurysm_problem(args.adjoint_n, q=ADJOINT["q"], seed=ADJOINT["seed"])
+    T, K = args.adjoint_T, args.adjoint_K
+    sim = lbm.Simulation(prob)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        out = None
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return min(ts), out
+
+    for _ in range(args.warmup):
+        sim.step(T)
+    t_fwd, _ = timed(lambda: sim.step(T), 3)
+    reg = np.ascontiguousarray(prob.region, dtype=np.uint8)
+    grad = torch.empty(prob.flags.shape, dtype=torch.float64, device="cuda")
+    res = {"workload": f"aneurysm{args.adjoint_n} D3Q27 FP32, {prob.n_fluid} fluid cells, J = time-and-sac mean of "
+                       f"rho|u|^2/2 over steps 1..{T}, gradient w.r.t. porosity",
+           "T": T, "forward_s": t_fwd, "forward_step_us": 1e6 * t_fwd / T}
+    variants = [("checkpointed", K)] + ([] if args.no_full_history else [("full_history", T)])
+    for name, k in variants:
+        nbytes = lbm.lbm_adjoint_workspace_size(sim.ctx, T, k)
+        free, _ = torch.cuda.mem_get_info()
+        if nbytes > 0.8 * free:
+            res[name] = {"K": k, "skipped": f"needs {nbytes / 1e9:.1f} GB"}
+            continue
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        run = lambda: lbm.lbm_adjoint(sim.ctx, T, k, reg.ctypes.data, 0, ws.data_ptr(), nbytes, grad.data_ptr())
+        run()
+        t_adj, J = timed(run, 3)
+        res[name] = {"K": k, "seconds": t_adj, "cost_vs_forward": t_adj / t_fwd, "J": J,
+                     "workspace_gb": nbytes / 1e9}
+        del ws
+    sim.close()
+    return res
 
 
 def cpu_baseline(prob, sim_factory=None, sample_steps=40):
@@ -363,6 +423,14 @@ def main():
     ap.add_argument("--ref-sample-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the other storage types")
+    ap.add_argument("--no-full-history", action="store_true", help="skip the adjoint with K = T")
+    ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="aneurysm box edge")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16dev", "bf16dev"])
+    ap.add_argument("--adjoint-n", type=int, default=ADJOINT["n"])
+    ap.add_argument("--adjoint-T", type=int, default=ADJOINT["T"])
+    ap.add_argument("--adjoint-K", type=int, default=ADJOINT["K"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: warm-up raised to 3 (timing rule)", file=sys.stderr)
