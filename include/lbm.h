@@ -97,13 +97,17 @@ typedef struct {
     double rho_out;
 } lbm_bc;
 
-/* Length of the internal cell list for these flags (host memory): every
- * non-solid cell plus the solid cells that share an aligned 16-cell group with
- * a bulk fluid cell (those receive full-sector zero stores).  -1 on bad input. */
+/* Length of the packed layout for these flags (host memory): the library
+ * stores, for every x-row (y, z) of the box, the span from the first to the
+ * last non-solid cell of that row, and packs these spans back to back; the
+ * result is the sum of the span lengths (non-solid cells plus the solid cells
+ * inside spans).  -1 on bad input. */
 int64_t lbm_list_length(const lbm_grid* grid, const uint8_t* flags);
 
-/* Bytes of device workspace for a cell list of n_list entries (from
- * lbm_list_length; pass n_list < 0 for the bound nx*ny*nz).  0 on a bad grid. */
+/* Bytes of device workspace for a packed layout of n_list slots (from
+ * lbm_list_length; pass n_list < 0 for the bound nx*ny*nz).  The distribution
+ * buffers take 2 Q n_list elements; the rest is per-box (flags, porosity,
+ * region: 6 bytes per box cell) and per-row.  0 on a bad grid. */
 size_t lbm_workspace_size(const lbm_grid* grid, int64_t n_list);
 
 /* Creates a context and sets the initial state (Sec. 3, Sec. 4):
@@ -152,8 +156,10 @@ lbm_status lbm_diag(lbm_ctx* ctx, const uint8_t* region, int32_t region_on_devic
  * call allocates nothing.  It is meant for callers that may not allocate
  * device memory where they need the diagnostics, e.g. a monitoring thread of a
  * host application whose device allocator is owned by another framework.
- *  - Limit: at most 8,388,608 non-solid cells (LBM_EINVAL beyond, use lbm_diag);
- *    the array costs every GPU that loads the library 2.25 MiB until exit.
+ *  - Limit: at most 8,388,608 slots of the packed layout (lbm_list_length)
+ *    and 1,048,576 cells on periodic faces, inlet or outlet (LBM_EINVAL
+ *    beyond, use lbm_diag);
+ *    the array costs every GPU that loads the library 4.5 MiB until exit.
  *  - region: device memory or NULL (host regions are rejected with LBM_EINVAL,
  *    since copying them would need scratch); out: host memory; synchronises.
  *  - The context's device must be current.  The first call on a device looks

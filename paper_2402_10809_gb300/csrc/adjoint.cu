@@ -36,9 +36,8 @@ cudaError_t LBM_LAUNCHER(int what, const AdjParams& A, cudaStream_t s)
         if (grid == 0) return cudaSuccess;
         adjoint_kernel<LBM_Q, LBM_T><<<grid, kBlock, 0, s>>>(A);
     } else {
-        const int n = A.F.n_cells - A.F.n_bulk;
-        if (n == 0) return cudaSuccess;
-        adjoint_outlet_fixup<LBM_Q><<<(n + 127) / 128, 128, 0, s>>>(A);
+        if (A.n_out == 0) return cudaSuccess;
+        adjoint_outlet_fixup<LBM_Q><<<(A.n_out + 127) / 128, 128, 0, s>>>(A);
     }
     return cudaGetLastError();
 }

@@ -9,8 +9,8 @@
 // time t applied).  The objective is
 //     J = kappa sum_{t=1..T} sum_{y in R} rho(t, y) |u(t, y)|^2 / 2,
 // kappa = 1 / (T |R|), with rho and u from f(t) as in the collision of time t.
-// The adjoint states are lambda(t) = dJ/dS(t) (FP32, same [Q][N] layout) and
-// mu(t) = dJ/domega(t) (list order).
+// The adjoint states are lambda(t) = dJ/dS(t) (FP32, same [Q][n_store] layout) and
+// mu(t) = dJ/domega(t) (per slot).
 //
 // The pull of step t reads every slot of S(t-1) exactly once (normal pull by
 // y + c_i, or the cell's own bounce-back), so its transpose is a permutation:
@@ -22,7 +22,8 @@
 //  * the extrapolation outlet reads its interior neighbour's pulled values;
 //    its contributions go to a small per-outlet buffer that a fix-up kernel
 //    adds to the neighbour's source slots after the main kernel.
-// dJ/dphi accumulates in FP64 in a dense [N] array owned by the caller.
+// dJ/dphi accumulates in FP64 per slot; the host scatters it to the caller's
+// dense array at the end.
 #pragma once
 
 #include "kernels.cuh"
@@ -31,20 +32,33 @@ namespace lbm {
 
 struct AdjParams {
     Params F;               // forward parameters: F.fsrc = S(t-1), F.omega = omega(t-1), F.t = t
-    const float* lam_in;    // lambda(t) [Q][N] (not read when first)
-    float* lam_out;         // lambda(t-1) [Q][N] (not written when last)
-    float* mu;              // [n_cells]: mu(t) in, mu(t-1) out
-    const float* drho_prev; // dense rho(t-1) - 1: porosity-link gather (not read when last)
-    double* gphi;           // dense dJ/dphi, accumulated
+    const float* lam_in;    // lambda(t) [Q][n_store] (not read when first)
+    float* lam_out;         // lambda(t-1) [Q][n_store] (not written when last)
+    float* mu;              // [n_store]: mu(t) in, mu(t-1) out
+    const float* drho_prev; // [n_store] rho(t-1) - 1: porosity-link gather (not read when last)
+    double* gphi;           // [n_store] dJ/dphi, accumulated
     const uint8_t* region;  // dense objective region R
     float kappa;            // 1 / (T |R|)
     int first;              // t = T: no collision of time t in the objective's history
     int objective;          // t >= 1: the kinetic-energy term of time t belongs to J
     int last;               // t = 0: S(-1) and omega(-1) are constants
-    float* bnd_delta;       // [Q][n_cells - n_bulk]: outlet contributions to the neighbour's slots
-    double* bnd_dphi;       // [n_cells - n_bulk]: outlet contribution to the neighbour's porosity
+    const uint32_t* out_slots;  // [n_out] slots of the outlet cells, ascending
+    int n_out;
+    float* bnd_delta;       // [Q][n_out]: outlet contributions to the neighbour's slots
+    double* bnd_dphi;       // [n_out]: outlet contribution to the neighbour's porosity
     double* jpart;          // [blocks]: per-block sums of the objective (accumulated over launches)
 };
+
+// Ordinal of outlet slot p in the ascending outlet list.
+__device__ __forceinline__ int outlet_ordinal(const AdjParams& A, int p)
+{
+    int lo = 0, hi = A.n_out - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)A.out_slots[mid] < p) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
 
 // ------------------------------------------------------------------ pieces
 
@@ -207,21 +221,22 @@ __device__ __forceinline__ void zou_he_adjoint(const Params& P, float prof, vola
 // populations and phi).  The neighbour's part is stored for the fix-up kernel;
 // the unknown slots of this cell end at zero.
 template <int Q, class T>
-__device__ __forceinline__ void outlet_adjoint(const AdjParams& A, const Coords& c, float phi, int q,
+__device__ __forceinline__ void outlet_adjoint(const AdjParams& A, const Coords& c, float phi, int p,
                                                volatile float* park, float& phib)
 {
     using L = Lattice<Q>;
     const Params& P = A.F;
     const int ax = P.out_axis;
     const int sgn = P.out_side == 1 ? -1 : 1;
-    const uint32_t nbmask = P.bnd_nbmask[q];
+    const uint32_t nbmask = P.bnd_nbmask[p];
+    const int q = outlet_ordinal(A, p);
     const Coords nc = make_coords(P, c.x + (ax == 0 ? sgn : 0), c.y + (ax == 1 ? sgn : 0), c.z + (ax == 2 ? sgn : 0));
-    const float phin = __ldg(P.phi + nc.idx);
+    const float phin = __ldg(P.phi + nc.slot);
     const T* f = static_cast<const T*>(P.fsrc);
     float sd = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const float v = Store<T>::ld(f + pull_offset<Q>(P.N, nc, nbmask, i));
+        const float v = Store<T>::ld(f + pull_offset<Q>(P, nc, nbmask, i));
         sd += v;
         if (L::cx(i)) mx += L::cx(i) > 0 ? v : -v;
         if (L::cy(i)) my += L::cy(i) > 0 ? v : -v;
@@ -252,7 +267,7 @@ __device__ __forceinline__ void outlet_adjoint(const AdjParams& A, const Coords&
     }
     float mbx, mby, mbz, phinb = 0.0f;
     const float sdb = macro_adjoint(P, phin, mx, my, mz, M, b, mbx, mby, mbz, phinb);
-    const int nb_count = P.n_cells - P.n_bulk;
+    const int nb_count = A.n_out;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         float d = sdb;
@@ -275,35 +290,39 @@ __device__ __forceinline__ void outlet_adjoint(const AdjParams& A, const Coords&
 // populations and write them to lambda(t-1) at the source slots; add the
 // cell's dJ/dphi terms; write mu(t-1).  jv accumulates the objective term.
 template <int Q, class T, bool fast>
-__device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t idx, uint32_t mask,
-                                             volatile float* park, double& jv)
+__device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t mask, volatile float* park,
+                                             double& jv)
 {
     using L = Lattice<Q>;
     const Params& P = A.F;
-    if (fast && (idx & 0x80000000u)) return;  // ghost entry: no state
-    const float phi = __ldg(P.phi + idx);
+    const float phi = __ldg(P.phi + p);
     const T* __restrict__ fs = static_cast<const T*>(P.fsrc);
-    const uint32_t N = (uint32_t)P.N;
-    const int sy = P.nx, sz = P.nx * P.ny;
+    const uint32_t n = (uint32_t)P.n_store;
     int type = kBulk;
     Coords cg;
+    RowBases rb;
+    int x = 0;
+    uint32_t row = 0;
     {
         float g[Q];
         if (fast) {
+            row = P.rows[p];
+            rb = row_bases(P, row);
+            x = p - rb.b[4];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const uint32_t d = (uint32_t)(L::cx(i) + L::cy(i) * sy + L::cz(i) * sz);
-                const uint32_t o = ((mask >> i) & 1u) ? (uint32_t)opp(i) * N + idx : (uint32_t)i * N + idx - d;
+                const uint32_t o = ((mask >> i) & 1u) ? (uint32_t)opp(i) * n + (uint32_t)p
+                                                      : (uint32_t)i * n + lean_slot(rb, x, -L::cx(i), -L::cy(i), -L::cz(i));
                 g[i] = Store<T>::ld(fs + o);
             }
         } else {
-            cg = coords_of(P, idx);
-            pull_general<Q, T>(fs, P.N, cg, mask, g);
+            cg = coords_of(P, p);
+            pull_general<Q, T>(P, fs, cg, mask, g);
             type = (mask >> kTypeShift) & 3u;
             if (type == kInlet) {
-                zou_he<Q>(P, P.bnd_prof[p - P.n_bulk], g);
+                zou_he<Q>(P, P.bnd_prof[p], g);
             } else if (type == kOutlet) {
-                outlet<Q, T>(P, cg, phi, P.bnd_nbmask[p - P.n_bulk], g);
+                outlet<Q, T>(P, cg, phi, P.bnd_nbmask[p], g);
             }
         }
 #pragma unroll
@@ -335,8 +354,8 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     const float irho = __fdividef(1.0f, M.rho);
     const float gdot = 3.0f * om_prev * pn * irho;
     // Carreau-Yasuda viscosity and rate with the pieces of their derivatives
-    const float x = P.lam * gdot;
-    const float xa = P.cy_a_two ? x * x : __powf(x, P.cy_a);
+    const float lx = P.lam * gdot;
+    const float xa = P.cy_a_two ? lx * lx : __powf(lx, P.cy_a);
     const float base = 1.0f + xa;
     const float pw = exp2f(P.cy_e * __log2f(base));
     const float mu = fmaf(P.mu0 - P.mu_inf, pw, P.mu_inf);
@@ -350,13 +369,13 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     MacroBar b{};
     float omb = 0.0f, phib = 0.0f;
     if (!A.first) {
-        const float* __restrict__ la = A.lam_in + idx;
+        const float* __restrict__ la = A.lam_in + p;
         float h[Q];
         float Ag = 0.0f, Wd = 0.0f, Aphi = 0.0f;
         const bool porous = (mask & kPorousBit) != 0u;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float a = __ldcs(la + (size_t)i * N);
+            const float a = __ldcs(la + (size_t)i * n);
             Ag = fmaf(a, park[i * kBlock], Ag);
             park[i * kBlock] = a;
             h[i] = L::w(i) * a;
@@ -367,9 +386,9 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
                 if (porous) {
                     uint32_t ni;
                     if (fast)
-                        ni = idx + (uint32_t)(L::cx(i) + L::cy(i) * sy + L::cz(i) * sz);
+                        ni = lean_slot(rb, x, L::cx(i), L::cy(i), L::cz(i));
                     else
-                        ni = (uint32_t)shifted(cg, L::cx(i), L::cy(i), L::cz(i));
+                        ni = (uint32_t)shifted(P, cg, L::cx(i), L::cy(i), L::cz(i));
                     Aphi = fmaf(h[i], __ldg(P.phi + ni) - phi, Aphi);
                 }
             }
@@ -418,7 +437,7 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     const float mub = -omb * 12.0f * M.rho * iE * iE;
     // mu = mu_inf + (mu0 - mu_inf)(1 + x^a)^((n-1)/a):
     // dmu/dx = (mu0 - mu_inf)(n - 1)(1 + x^a)^((n-1)/a - 1) x^(a-1)
-    const float xam1 = P.cy_a_two ? x : (x > 0.0f ? __fdividef(xa, x) : 0.0f);
+    const float xam1 = P.cy_a_two ? lx : (lx > 0.0f ? __fdividef(xa, lx) : 0.0f);
     const float dmudx = (P.mu0 - P.mu_inf) * (P.cy_e * P.cy_a) * __fdividef(pw, base) * xam1;
     const float gdb = P.lam * mub * dmudx;
     // gdot = 3 omega(t-1) |Pi| / rho
@@ -426,7 +445,7 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     const float pnb = gdb * 3.0f * om_prev * irho;
     b.rho -= gdb * gdot * irho;
     // objective term of time t
-    if (A.objective && A.region[idx]) {
+    if (A.objective && A.region[fast ? (long long)x + (long long)P.nx * row : cg.idx]) {
         const float uu = fmaf(M.ux, M.ux, fmaf(M.uy, M.uy, M.uz * M.uz));
         jv += (double)A.kappa * 0.5 * (double)M.rho * (double)uu;
         b.rho = fmaf(0.5f * A.kappa, uu, b.rho);
@@ -478,9 +497,9 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     }
     if (!fast) {
         if (type == kInlet) {
-            zou_he_adjoint<Q>(P, P.bnd_prof[p - P.n_bulk], park, phib);
+            zou_he_adjoint<Q>(P, P.bnd_prof[p], park, phib);
         } else if (type == kOutlet) {
-            outlet_adjoint<Q, T>(A, cg, phi, p - P.n_bulk, park, phib);
+            outlet_adjoint<Q, T>(A, cg, phi, p, park, phib);
         }
     }
 
@@ -495,26 +514,27 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
             const float v = park[i * kBlock];
             const bool bb = ((mask >> i) & 1u) != 0u;
             if (fast) {
-                const uint32_t d = (uint32_t)(L::cx(i) + L::cy(i) * sy + L::cz(i) * sz);
-                lo[bb ? (uint32_t)opp(i) * N + idx : (uint32_t)i * N + idx - d] = v;
-                if (!bb && i != 0) gat = fmaf(L::w(i) * __ldg(A.drho_prev + (idx - d)), v, gat);
+                const uint32_t src = lean_slot(rb, x, -L::cx(i), -L::cy(i), -L::cz(i));
+                lo[bb ? (uint32_t)opp(i) * n + (uint32_t)p : (uint32_t)i * n + src] = v;
+                if (!bb && i != 0) gat = fmaf(L::w(i) * __ldg(A.drho_prev + src), v, gat);
             } else {
-                lo[pull_offset<Q>(P.N, cg, mask, i)] = v;
+                lo[pull_offset<Q>(P, cg, mask, i)] = v;
                 if (!bb && i != 0)
-                    gat = fmaf(L::w(i) * __ldg(A.drho_prev + shifted(cg, -L::cx(i), -L::cy(i), -L::cz(i))), v, gat);
+                    gat = fmaf(L::w(i) * __ldg(A.drho_prev + shifted(P, cg, -L::cx(i), -L::cy(i), -L::cz(i))), v,
+                               gat);
             }
         }
         gacc += (double)gat;
         A.mu[p] = mu_prev;
     }
-    A.gphi[idx] += gacc;
+    A.gphi[p] += gacc;
 }
 
 template <int Q, class T>
-__device__ __noinline__ void adjoint_general(const AdjParams& A, int p, uint32_t idx, uint32_t mask,
-                                             volatile float* park, double& jv)
+__device__ __noinline__ void adjoint_general(const AdjParams& A, int p, uint32_t mask, volatile float* park,
+                                             double& jv)
 {
-    adjoint_cell<Q, T, false>(A, p, idx, mask, park, jv);
+    adjoint_cell<Q, T, false>(A, p, mask, park, jv);
 }
 
 template <int Q, class T>
@@ -522,18 +542,22 @@ __global__ void __launch_bounds__(kBlock, 2) adjoint_kernel(const AdjParams A)
 {
     const Params& P = A.F;
     const int nbg = general_blocks(P);
-    const bool fast = (int)blockIdx.x >= nbg;
-    const int p = fast ? ((int)blockIdx.x - nbg) * kBlock + (int)threadIdx.x
-                       : P.n_fast + (int)blockIdx.x * kBlock + (int)threadIdx.x;
-    const int pend = fast ? P.n_fast : P.n_cells;
     __shared__ float sg[Q * kBlock];
     volatile float* park = sg + threadIdx.x;
     double jv = 0.0;
-    if (p < pend) {
-        if (fast)
-            adjoint_cell<Q, T, true>(A, p, P.cells[p], P.mask[p], park, jv);
-        else
-            adjoint_general<Q, T>(A, p, P.cells[p], P.mask[p], park, jv);
+    if ((int)blockIdx.x < nbg) {
+        const int k = (int)blockIdx.x * P.gen_block + (int)threadIdx.x;
+        if ((int)threadIdx.x < P.gen_block && k < P.n_general) {
+            const int p = (int)P.general[k];
+            adjoint_general<Q, T>(A, p, P.mask[p], park, jv);
+        }
+    } else {
+        const int p = ((int)blockIdx.x - nbg) * kBlock + (int)threadIdx.x;
+        if (p < P.n_store) {
+            const uint32_t mask = P.mask[p];
+            // ghost slots hold no state; general cells belong to the general blocks
+            if (!(mask & (kGhostBit | kGeneralBits)) && !P.wide) adjoint_cell<Q, T, true>(A, p, mask, park, jv);
+        }
     }
     if (A.objective) {
         // block sum of the objective terms, added to this block's running partial
@@ -552,35 +576,33 @@ __global__ void __launch_bounds__(kBlock, 2) adjoint_kernel(const AdjParams A)
 
 // Fix-up after adjoint_kernel: adds each outlet's contributions to its interior
 // neighbour's source slots of lambda(t-1) (with the porosity-link gather those
-// slots carry) and to the neighbour's porosity.  One thread per boundary entry.
+// slots carry) and to the neighbour's porosity.  One thread per outlet cell.
 template <int Q>
 __global__ void adjoint_outlet_fixup(const AdjParams A)
 {
     using L = Lattice<Q>;
     const Params& P = A.F;
-    const int nbc = P.n_cells - P.n_bulk;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nbc) return;
-    const int p = P.n_bulk + q;
-    if ((((uint32_t)P.mask[p] >> kTypeShift) & 3u) != kOutlet) return;
-    const Coords c = coords_of(P, P.cells[p]);
+    if (q >= A.n_out) return;
+    const int p = (int)A.out_slots[q];
+    const Coords c = coords_of(P, p);
     const int ax = P.out_axis;
     const int sgn = P.out_side == 1 ? -1 : 1;
     const Coords nc = make_coords(P, c.x + (ax == 0 ? sgn : 0), c.y + (ax == 1 ? sgn : 0), c.z + (ax == 2 ? sgn : 0));
-    const uint32_t nbmask = P.bnd_nbmask[q];
+    const uint32_t nbmask = P.bnd_nbmask[p];
     double acc = A.bnd_dphi[q];
     if (!A.last) {
         float gat = 0.0f;
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
-            const float d = A.bnd_delta[(size_t)j * nbc + q];
-            A.lam_out[pull_offset<Q>(P.N, nc, nbmask, j)] += d;
+            const float d = A.bnd_delta[(size_t)j * A.n_out + q];
+            A.lam_out[pull_offset<Q>(P, nc, nbmask, j)] += d;
             if (j != 0 && !((nbmask >> j) & 1u))
-                gat = fmaf(L::w(j) * A.drho_prev[shifted(nc, -L::cx(j), -L::cy(j), -L::cz(j))], d, gat);
+                gat = fmaf(L::w(j) * A.drho_prev[shifted(P, nc, -L::cx(j), -L::cy(j), -L::cz(j))], d, gat);
         }
         acc += (double)gat;
     }
-    A.gphi[nc.idx] += acc;
+    A.gphi[nc.slot] += acc;
 }
 
 }  // namespace lbm

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -34,17 +35,18 @@ using namespace lbm;
 
 namespace {
 
-constexpr uint64_t kStateMagic = 0x314d425356414e45ull;  // checkpoint header tag
+constexpr uint64_t kStateMagic = 0x324d425356414e45ull;  // checkpoint header tag (packed layout)
 constexpr size_t kHeader = 256;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t elem_size(int storage) { return storage == LBM_F32 ? 4 : 2; }
 
+// Workspace layout.  The fixed part depends on the box only; the slot part on
+// the number of slots of the packed layout (lbm_list_length).
 struct Layout {
-    size_t f[2], phi, flags, region, counts, offsets, totals, err, diag_out;
-    size_t cells, mask, omega, bnd_prof, bnd_nbmask, partials, staging, pack, end;
-    size_t fixed_end;
+    size_t flags, phi_dense, region, xmin, ext, rowbase, rownb, err, diag_out, fixed_end;
+    size_t rows, mask, omega, phi, bnd_prof, bnd_nbmask, general, partials, staging, f[2], end;
 };
 
 bool grid_ok(const lbm_grid* g)
@@ -58,34 +60,36 @@ bool grid_ok(const lbm_grid* g)
     return true;
 }
 
-Layout layout(const lbm_grid* g, long long nf)
+Layout layout(const lbm_grid* g, long long n_store)
 {
     Layout L{};
-    const long long N = (long long)g->nx * g->ny * g->nz;
-    const size_t fb = (size_t)g->q * (size_t)N * elem_size(g->storage);
-    const long long nblk = (N + kSetupChunk - 1) / kSetupChunk;
+    const size_t N = (size_t)g->nx * g->ny * g->nz;
+    const size_t nrows = (size_t)g->ny * g->nz;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
-    L.f[0] = take(fb);
-    L.f[1] = take(fb);
-    L.phi = take((size_t)N * 4);
-    L.flags = take((size_t)N);
-    L.region = take((size_t)N);
-    L.counts = take((size_t)nblk * kCounters * 4);
-    L.offsets = take((size_t)nblk * kCategories * 4);
-    L.totals = take(kCounters * 4);
+    L.flags = take(N);
+    L.phi_dense = take(N * 4);
+    L.region = take(N);
+    L.xmin = take(nrows * 4);
+    L.ext = take(nrows * 4);
+    L.rowbase = take(nrows * 4);
+    L.rownb = take(nrows * 48);
     L.err = take(32);
     L.diag_out = take(8 * 8);
     L.fixed_end = o;
-    const size_t n = (size_t)(nf > 0 ? nf : 1);
-    L.cells = take(n * 4);
+    const size_t n = (size_t)(n_store > 0 ? n_store : 1);
+    L.rows = take(n * 4);
     L.mask = take(n * 4);
     L.omega = take(n * 4);
+    L.phi = take(n * 4);
     L.bnd_prof = take(n * 4);
     L.bnd_nbmask = take(n * 4);
-    L.partials = take(((n + kBlock - 1) / kBlock + 1) * kDiagSlots * 8);  // fast + general block ranges
+    L.general = take(n * 4);
+    L.partials = take(((n + 31) / 32 + (n + kBlock - 1) / kBlock + 1) * kDiagSlots * 8);  // general + lean blocks
     L.staging = take(n * 6 * 4);
-    L.pack = take(n * ((size_t)g->q * elem_size(g->storage) + 4));
+    const size_t fb = (size_t)g->q * n * elem_size(g->storage);
+    L.f[0] = take(fb);
+    L.f[1] = take(fb);
     L.end = o;
     return L;
 }
@@ -102,6 +106,31 @@ cudaError_t launch(const lbm_grid& g, int mode, const Params& P, cudaStream_t s)
     return launch_step_27_bf16(mode, P, s);
 }
 
+// Spans of the non-solid cells of every row (host form of setup_rows).
+long long host_spans(const lbm_grid* g, const uint8_t* flags, std::vector<int>* xmin, std::vector<int>* ext)
+{
+    const long long nx = g->nx, nrows = (long long)g->ny * g->nz;
+    long long total = 0;
+    if (xmin) xmin->assign(nrows, 0);
+    if (ext) ext->assign(nrows, 0);
+    for (long long r = 0; r < nrows; ++r) {
+        const uint8_t* row = flags + r * nx;
+        long long lo = -1, hi = -1;
+        for (long long x = 0; x < nx; ++x) {
+            if (row[x] >= 1 && row[x] <= 3) {
+                if (lo < 0) lo = x;
+                hi = x;
+            }
+        }
+        if (lo >= 0) {
+            total += hi - lo + 1;
+            if (xmin) (*xmin)[r] = (int)lo;
+            if (ext) (*ext)[r] = (int)(hi - lo + 1);
+        }
+    }
+    return total;
+}
+
 }  // namespace
 
 struct lbm_ctx {
@@ -114,8 +143,9 @@ struct lbm_ctx {
     size_t ws_bytes = 0;
     Layout L{};
     long long N = 0;
-    int n_cells = 0, n_fast = 0, n_bulk = 0, n_in = 0, n_out = 0;
-    int n_ghost = 0;  // ghost entries among the n_fast cells of group 0
+    int n_store = 0;                  // slots of the packed layout
+    int n_ghost = 0;                  // ghost slots among them
+    int n_in = 0, n_out = 0;
     int cur = 0;
     long long t = 0;
     int check_every = 0;
@@ -123,7 +153,9 @@ struct lbm_ctx {
     long long since_check = 0;
     float omega0 = 1.0f;
     Params base{};
-    std::vector<uint32_t> host_cells;
+    std::vector<long long> host_idx;  // dense index of each slot, -1 for ghost slots
+    std::vector<uint32_t> out_slots;  // slots of the outlet cells
+    std::vector<uint32_t> general;    // slots of the general-path cells
     std::string err;
 
     template <class T>
@@ -155,33 +187,11 @@ extern "C" size_t lbm_workspace_size(const lbm_grid* grid, int64_t n_list)
     return layout(grid, n_list < 0 ? N : (n_list > N ? N : n_list)).end;
 }
 
-// Host mirror of the set-up's list rule: every non-solid cell, plus each solid
-// cell of an aligned 16-cell group that holds a bulk cell off periodic faces.
+// Host mirror of the set-up's layout: the total length of the row spans.
 extern "C" int64_t lbm_list_length(const lbm_grid* grid, const uint8_t* flags)
 {
     if (!grid_ok(grid) || !flags) return -1;
-    const long long nx = grid->nx, ny = grid->ny, nz = grid->nz, N = nx * ny * nz;
-    auto periodic_face = [&](long long idx) {
-        const long long z = idx / (nx * ny), r = idx - z * nx * ny, y = r / nx, x = r - y * nx;
-        return (grid->periodic[0] && (x == 0 || x == nx - 1)) || (grid->periodic[1] && (y == 0 || y == ny - 1)) ||
-               (grid->periodic[2] && (z == 0 || z == nz - 1));
-    };
-    int64_t n = 0;
-    for (long long g0 = 0; g0 < N; g0 += kGhostGroup) {
-        const long long g1 = g0 + kGhostGroup < N ? g0 + kGhostGroup : N;
-        bool bulk = false;
-        int64_t listed = 0, solid = 0;
-        for (long long i = g0; i < g1; ++i) {
-            if (flags[i] == LBM_SOLID) {
-                ++solid;
-            } else if (flags[i] <= LBM_OUTLET) {
-                ++listed;
-                if (flags[i] == LBM_FLUID && !bulk && !periodic_face(i)) bulk = true;
-            }
-        }
-        n += listed + (bulk ? solid : 0);
-    }
-    return n;
+    return host_spans(grid, flags, nullptr, nullptr);
 }
 
 static lbm_status run_diag(lbm_ctx* c, const uint8_t* region_dev, double out[8])
@@ -236,47 +246,83 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     c->ws_bytes = workspace_bytes;
     c->N = (long long)grid->nx * grid->ny * grid->nz;
     c->L = layout(grid, 0);
-    if (workspace_bytes < c->L.end) return fail(c, LBM_ENOMEM, "workspace smaller than lbm_workspace_size(grid, 0)");
+    if (workspace_bytes < c->L.fixed_end)
+        return fail(c, LBM_ENOMEM, "workspace smaller than lbm_workspace_size(grid, 0)");
+    const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+    const int nrows = ny * nz;
 
     const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     LBM_CUDA(cudaMemcpyAsync(c->at<uint8_t>(c->L.flags), flags, (size_t)c->N, kind, c->stream), "copy flags");
-    LBM_CUDA(cudaMemcpyAsync(c->at<float>(c->L.phi), porosity, (size_t)c->N * 4, kind, c->stream), "copy porosity");
+    LBM_CUDA(cudaMemcpyAsync(c->at<float>(c->L.phi_dense), porosity, (size_t)c->N * 4, kind, c->stream),
+             "copy porosity");
+    uint32_t* errw = c->at<uint32_t>(c->L.err);
+    LBM_CUDA(cudaMemsetAsync(errw, 0, 32, c->stream), "clear error words");
 
-    // cell list: count, scan, emit
-    CellGrid CG{grid->nx, grid->ny, grid->nz, {grid->periodic[0] ? 1 : 0, grid->periodic[1] ? 1 : 0,
-                                                grid->periodic[2] ? 1 : 0}};
-    LBM_CUDA(launch_setup_cells(c->at<uint8_t>(c->L.flags), c->N, CG, c->at<uint32_t>(c->L.counts),
-                                c->at<uint32_t>(c->L.offsets), c->at<uint32_t>(c->L.totals), c->stream, 0, nullptr),
-             "setup count");
-    uint32_t tot[kCounters] = {0, 0, 0, 0, 0};
-    LBM_CUDA(cudaMemcpyAsync(tot, c->at<uint32_t>(c->L.totals), sizeof(tot), cudaMemcpyDeviceToHost, c->stream),
-             "copy totals");
+    // row spans (device), scanned on the host into the row bases
+    LBM_CUDA(launch_setup_rows(c->at<uint8_t>(c->L.flags), nx, nrows, c->at<int>(c->L.xmin), c->at<int>(c->L.ext),
+                               errw, c->stream),
+             "setup_rows");
+    std::vector<int> xmin(nrows), ext(nrows);
+    uint32_t err0 = 0;
+    LBM_CUDA(cudaMemcpyAsync(xmin.data(), c->at<int>(c->L.xmin), (size_t)nrows * 4, cudaMemcpyDeviceToHost, c->stream),
+             "copy spans");
+    LBM_CUDA(cudaMemcpyAsync(ext.data(), c->at<int>(c->L.ext), (size_t)nrows * 4, cudaMemcpyDeviceToHost, c->stream),
+             "copy spans");
+    LBM_CUDA(cudaMemcpyAsync(&err0, errw, 4, cudaMemcpyDeviceToHost, c->stream), "copy error word");
     LBM_CUDA(cudaStreamSynchronize(c->stream), "setup sync");
-    c->n_fast = (int)tot[0];
-    c->n_bulk = (int)(tot[0] + tot[1]);
-    c->n_in = (int)tot[2];
-    c->n_out = (int)tot[3];
-    c->n_ghost = (int)tot[4];
-    c->n_cells = c->n_bulk + c->n_in + c->n_out;
-    c->L = layout(grid, c->n_cells);
+    if (err0 & kErrFlag) return fail(c, LBM_EINVAL, "flags must be 0 (solid), 1 (fluid), 2 (inlet) or 3 (outlet)");
+    long long total = 0;
+    std::vector<int> rowbase(nrows, 0);
+    for (int r = 0; r < nrows; ++r) {
+        if (ext[r] > 0) {
+            if (total - xmin[r] < INT32_MIN || total + nx > INT32_MAX)
+                return fail(c, LBM_EINVAL, "too many non-solid cells for 32-bit slot indices");
+            rowbase[r] = (int)(total - xmin[r]);
+        }
+        total += ext[r];
+    }
+    c->n_store = (int)total;
+    c->L = layout(grid, c->n_store);
     if (workspace_bytes < c->L.end)
-        return fail(c, LBM_ENOMEM, "workspace smaller than lbm_workspace_size(grid, " + std::to_string(c->n_cells) +
-                                       "), the cell-list length of these flags");
-    LBM_CUDA(launch_setup_cells(c->at<uint8_t>(c->L.flags), c->N, CG, c->at<uint32_t>(c->L.counts),
-                                c->at<uint32_t>(c->L.offsets), c->at<uint32_t>(c->L.totals), c->stream, 1,
-                                c->at<uint32_t>(c->L.cells)),
-             "setup emit");
+        return fail(c, LBM_ENOMEM, "workspace smaller than lbm_workspace_size(grid, " + std::to_string(c->n_store) +
+                                       "), the packed length of these flags");
+    // per row: the bases of its nine neighbour rows, wrapped on periodic axes
+    // (0 outside the box: those links are never pulled), then y, z
+    std::vector<int> rownb((size_t)nrows * 12, 0);
+    for (int z = 0; z < nz; ++z) {
+        for (int y = 0; y < ny; ++y) {
+            const int r = y + ny * z;
+            int* e = &rownb[(size_t)r * 12];
+            for (int sz = -1; sz <= 1; ++sz)
+                for (int sy = -1; sy <= 1; ++sy) {
+                    int yy = y + sy, zz = z + sz;
+                    if (grid->periodic[1]) yy = (yy + ny) % ny;
+                    if (grid->periodic[2]) zz = (zz + nz) % nz;
+                    e[(sy + 1) + 3 * (sz + 1)] = (yy >= 0 && yy < ny && zz >= 0 && zz < nz) ? rowbase[yy + ny * zz] : 0;
+                }
+            e[9] = y;
+            e[10] = z;
+        }
+    }
+    LBM_CUDA(cudaMemcpyAsync(c->at<int>(c->L.rowbase), rowbase.data(), (size_t)nrows * 4, cudaMemcpyHostToDevice,
+                             c->stream), "copy row bases");
+    LBM_CUDA(cudaMemcpyAsync(c->at<int>(c->L.rownb), rownb.data(), (size_t)nrows * 48, cudaMemcpyHostToDevice,
+                             c->stream), "copy row table");
+    LBM_CUDA(launch_setup_slots(c->at<float>(c->L.phi_dense), nx, nrows, c->at<int>(c->L.rowbase),
+                                c->at<int>(c->L.xmin), c->at<int>(c->L.ext), c->at<uint32_t>(c->L.rows),
+                                c->at<float>(c->L.phi), c->stream),
+             "setup_slots");
 
     SetupParams S{};
-    S.nx = grid->nx;
-    S.ny = grid->ny;
-    S.nz = grid->nz;
+    S.nx = nx;
+    S.ny = ny;
+    S.nz = nz;
     for (int a = 0; a < 3; ++a) S.periodic[a] = grid->periodic[a] ? 1 : 0;
-    S.n_cells = c->n_cells;
-    S.n_bulk = c->n_bulk;
+    S.n_store = c->n_store;
     S.flags = c->at<uint8_t>(c->L.flags);
-    S.phi = c->at<float>(c->L.phi);
-    S.cells = c->at<uint32_t>(c->L.cells);
+    S.phi = c->at<float>(c->L.phi_dense);
+    S.rows = c->at<uint32_t>(c->L.rows);
+    S.rowbase = c->at<int>(c->L.rowbase);
     S.mask = c->at<uint32_t>(c->L.mask);
     S.bnd_prof = c->at<float>(c->L.bnd_prof);
     S.bnd_nbmask = c->at<uint32_t>(c->L.bnd_nbmask);
@@ -286,18 +332,19 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     S.out_side = bc->outlet_side;
     for (int a = 0; a < 3; ++a) S.in_center[a] = bc->inlet_center[a];
     S.in_radius = bc->inlet_radius;
-    S.err = c->at<uint32_t>(c->L.err);
-    LBM_CUDA(cudaMemsetAsync(S.err, 0, 32, c->stream), "clear error words");
+    S.err = errw;
     LBM_CUDA(launch_setup_mask(grid->q, S, c->stream), "setup_mask");
     uint32_t errv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    LBM_CUDA(cudaMemcpyAsync(errv, S.err, 32, cudaMemcpyDeviceToHost, c->stream), "copy error words");
-    c->host_cells.resize(c->n_cells);
-    if (c->n_cells > 0)
-        LBM_CUDA(cudaMemcpyAsync(c->host_cells.data(), S.cells, (size_t)c->n_cells * 4, cudaMemcpyDeviceToHost,
-                                 c->stream), "copy cell list");
+    LBM_CUDA(cudaMemcpyAsync(errv, errw, 32, cudaMemcpyDeviceToHost, c->stream), "copy error words");
+    std::vector<uint32_t> hmask(c->n_store), hrows(c->n_store);
+    if (c->n_store > 0) {
+        LBM_CUDA(cudaMemcpyAsync(hmask.data(), S.mask, (size_t)c->n_store * 4, cudaMemcpyDeviceToHost, c->stream),
+                 "copy masks");
+        LBM_CUDA(cudaMemcpyAsync(hrows.data(), S.rows, (size_t)c->n_store * 4, cudaMemcpyDeviceToHost, c->stream),
+                 "copy row ids");
+    }
     LBM_CUDA(cudaStreamSynchronize(c->stream), "setup sync");
-    const uint32_t errw = errv[0];
-    if (errw) {
+    if (errv[0]) {
         float bad_phi;
         std::memcpy(&bad_phi, &errv[3], 4);
         char where[256];
@@ -306,9 +353,9 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
                       errv[2] & 1023u, (errv[2] >> 10) & 1023u, errv[2] >> 20, (double)bad_phi,
                       (why & 1u) ? "; no inlet axis" : "", (why & 2u) ? "; inlet axis is periodic" : "",
                       (why & 4u) ? "; not on the inlet face" : "", (why & 8u) ? "; porosity is not 1" : "");
-        if (errw & kErrPorosity)
+        if (errv[0] & kErrPorosity)
             return fail(c, LBM_EINVAL, std::string("porosity must lie in (0, 1] on every non-solid cell") + where);
-        if (errw & kErrInlet)
+        if (errv[0] & kErrInlet)
             return fail(c, LBM_EINVAL,
                         std::string("inlet cells must lie on the inlet face, with an inlet configured and porosity 1") +
                             where);
@@ -316,6 +363,29 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
                     std::string("outlet cells must lie on the outlet face with porosity 1 and a fluid interior "
                                 "neighbour of porosity 1") + where);
     }
+    // host tables: dense index of every slot, ghost count, outlet slots
+    const bool wide = (unsigned long long)grid->q * (unsigned long long)c->n_store >= (1ull << 32);
+    c->host_idx.assign(c->n_store, -1);
+    c->out_slots.clear();
+    c->general.clear();
+    c->n_ghost = 0;
+    c->n_in = 0;
+    for (int p = 0; p < c->n_store; ++p) {
+        if (hmask[p] & kGhostBit) {
+            ++c->n_ghost;
+            continue;
+        }
+        const uint32_t r = hrows[p];
+        c->host_idx[p] = (long long)(p - rowbase[r]) + (long long)nx * r;
+        const uint32_t type = (hmask[p] >> kTypeShift) & 3u;
+        if (type == kOutlet) c->out_slots.push_back((uint32_t)p);
+        if (type == kInlet) ++c->n_in;
+        if (wide || (hmask[p] & kGeneralBits)) c->general.push_back((uint32_t)p);
+    }
+    c->n_out = (int)c->out_slots.size();
+    if (!c->general.empty())
+        LBM_CUDA(cudaMemcpyAsync(c->at<uint32_t>(c->L.general), c->general.data(), c->general.size() * 4,
+                                 cudaMemcpyHostToDevice, c->stream), "copy general list");
 
     // Lattice units from the Table 1 scales (Sec. 4): nu = mu / rho0 * dt / dx^2.
     const double scale = rheo->dt / (rheo->dx * rheo->dx);
@@ -323,18 +393,24 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     const double mui = rheo->mu_inf / rheo->rho0 * scale;
     const double nu_d = por->nu_darcy > 0 ? por->nu_darcy * scale : mu0;  // nu = mu0 / rho0 (Sec. 4)
     Params& P = c->base;
-    P.nx = grid->nx;
-    P.ny = grid->ny;
-    P.nz = grid->nz;
+    P.nx = nx;
+    P.ny = ny;
+    P.nz = nz;
     P.N = c->N;
-    P.n_cells = c->n_cells;
-    // the fast path indexes the distribution buffers with 32-bit element
-    // offsets; boxes beyond that run every cell through the general path
-    P.n_fast = (unsigned long long)grid->q * (unsigned long long)c->N < (1ull << 32) ? c->n_fast : 0;
-    P.n_bulk = c->n_bulk;
-    P.cells = S.cells;
+    P.n_store = c->n_store;
+    // the lean path indexes the distribution buffers with 32-bit element
+    // offsets; larger layouts run every cell through the general path
+    P.wide = wide ? 1 : 0;
+    P.n_general = (int)c->general.size();
+    // general cells per block: one warp's worth while the lean grid is under
+    // about four waves of 3 blocks on 152 SMs, full blocks beyond
+    P.gen_block = (c->n_store + kBlock - 1) / kBlock < 4 * 3 * 152 ? 32 : kBlock;
+    P.general = c->at<uint32_t>(c->L.general);
+    P.rows = S.rows;
+    P.rownb = c->at<int4>(c->L.rownb);
+    P.rowbase = S.rowbase;
     P.mask = S.mask;
-    P.phi = S.phi;
+    P.phi = c->at<float>(c->L.phi);
     P.bnd_prof = S.bnd_prof;
     P.bnd_nbmask = S.bnd_nbmask;
     P.gx = (float)bc->body_force[0];
@@ -370,9 +446,9 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     c->omega0 = (float)(2.0 / (6.0 * mu0 + 1.0));  // omega(mu0) at rho = 1
 
     // initial state: rest equilibrium (zero deviations)
-    LBM_CUDA(launch_init_state(grid->storage, S.cells, c->n_cells, grid->nx, grid->ny, c->N, grid->q, c->f(0), P.omega,
-                               c->omega0, c->stream),
-             "init_state");
+    const size_t fb = (size_t)grid->q * c->n_store * elem_size(grid->storage);
+    LBM_CUDA(cudaMemsetAsync(c->f(0), 0, fb, c->stream), "initial state");
+    LBM_CUDA(launch_fill_f32(P.omega, c->n_store, c->omega0, c->stream), "initial omega");
     c->cur = 0;
     c->t = 0;
     c->ready = true;
@@ -427,7 +503,7 @@ extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho, float* u, float* shear
         return launch(c->grid, kModeMoments, P, c->stream) == cudaSuccess ? LBM_OK
                                                                           : fail(c, LBM_ECUDA, "moments kernel");
     }
-    const size_t n = (size_t)c->n_cells;
+    const size_t n = (size_t)c->n_store;
     float* st = c->at<float>(c->L.staging);
     P.o_rho = st;
     P.o_ux = st + n;
@@ -447,7 +523,7 @@ extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho, float* u, float* shear
         if (!outs[k]) continue;
         std::memset(outs[k], 0, N * 4);
         for (size_t p = 0; p < n; ++p)
-            if (!(c->host_cells[p] & kGhostFlag)) outs[k][c->host_cells[p]] = h[k * n + p];
+            if (c->host_idx[p] >= 0) outs[k][c->host_idx[p]] = h[k * n + p];
     }
     return LBM_OK;
 }
@@ -482,24 +558,17 @@ namespace {
 struct StateHeader {
     uint64_t magic;
     int64_t t;
-    int64_t n_cells;
+    int64_t n_store;
     int32_t q, storage;
 };
 }  // namespace
 
+// Checkpoint: header, then the distributions [Q][n_store] in the storage type
+// and omega [n_store], both exactly as they sit in the workspace.
 extern "C" size_t lbm_state_size(const lbm_ctx* c)
 {
     if (!c || !c->ready) return 0;
-    return kHeader + (size_t)c->n_cells * ((size_t)c->grid.q * elem_size(c->grid.storage) + 4);
-}
-
-static lbm_status pack(lbm_ctx* c, int unpack, void* state)
-{
-    const lbm_grid& G = c->grid;
-    LBM_CUDA(launch_pack_state(G.storage, c->at<uint32_t>(c->L.cells), c->n_cells, G.nx, G.ny, c->N, G.q,
-                               c->f(c->cur), state, unpack, c->stream),
-             "pack_state");
-    return LBM_OK;
+    return kHeader + (size_t)c->n_store * ((size_t)c->grid.q * elem_size(c->grid.storage) + 4);
 }
 
 extern "C" lbm_status lbm_save(lbm_ctx* c, void* dst, size_t bytes, int32_t dst_on_device)
@@ -508,16 +577,12 @@ extern "C" lbm_status lbm_save(lbm_ctx* c, void* dst, size_t bytes, int32_t dst_
     if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
     const size_t need = lbm_state_size(c);
     if (bytes < need) return fail(c, LBM_ENOMEM, "destination smaller than lbm_state_size");
-    StateHeader h{kStateMagic, c->t, c->n_cells, c->grid.q, c->grid.storage};
-    char* pk = c->at<char>(c->L.pack);
-    const size_t fbytes = (size_t)c->n_cells * c->grid.q * elem_size(c->grid.storage);
-    lbm_status s = pack(c, 0, pk);
-    if (s != LBM_OK) return s;
-    LBM_CUDA(cudaMemcpyAsync(pk + fbytes, c->base.omega, (size_t)c->n_cells * 4, cudaMemcpyDeviceToDevice, c->stream),
-             "save omega");
+    StateHeader h{kStateMagic, c->t, c->n_store, c->grid.q, c->grid.storage};
+    const size_t fbytes = (size_t)c->n_store * c->grid.q * elem_size(c->grid.storage);
     const cudaMemcpyKind k = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     char* d = static_cast<char*>(dst);
-    LBM_CUDA(cudaMemcpyAsync(d + kHeader, pk, need - kHeader, k, c->stream), "save copy");
+    LBM_CUDA(cudaMemcpyAsync(d + kHeader, c->f(c->cur), fbytes, k, c->stream), "save state");
+    LBM_CUDA(cudaMemcpyAsync(d + kHeader + fbytes, c->base.omega, (size_t)c->n_store * 4, k, c->stream), "save omega");
     if (dst_on_device)
         LBM_CUDA(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream), "save header");
     LBM_CUDA(cudaStreamSynchronize(c->stream), "save sync");
@@ -539,24 +604,19 @@ extern "C" lbm_status lbm_load(lbm_ctx* c, const void* src, size_t bytes, int32_
     } else {
         std::memcpy(&h, s, sizeof(h));
     }
-    if (h.magic != kStateMagic || h.n_cells != c->n_cells || h.q != c->grid.q || h.storage != c->grid.storage)
+    if (h.magic != kStateMagic || h.n_store != c->n_store || h.q != c->grid.q || h.storage != c->grid.storage)
         return fail(c, LBM_EINVAL, "checkpoint does not match this context");
-    char* pk = c->at<char>(c->L.pack);
-    const size_t fbytes = (size_t)c->n_cells * c->grid.q * elem_size(c->grid.storage);
-    LBM_CUDA(cudaMemcpyAsync(pk, s + kHeader, need - kHeader,
-                             src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
-             "load copy");
-    lbm_status st = pack(c, 1, pk);
-    if (st != LBM_OK) return st;
-    LBM_CUDA(cudaMemcpyAsync(c->base.omega, pk + fbytes, (size_t)c->n_cells * 4, cudaMemcpyDeviceToDevice, c->stream),
-             "load omega");
+    const size_t fbytes = (size_t)c->n_store * c->grid.q * elem_size(c->grid.storage);
+    const cudaMemcpyKind k = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    LBM_CUDA(cudaMemcpyAsync(c->f(c->cur), s + kHeader, fbytes, k, c->stream), "load state");
+    LBM_CUDA(cudaMemcpyAsync(c->base.omega, s + kHeader + fbytes, (size_t)c->n_store * 4, k, c->stream), "load omega");
     LBM_CUDA(cudaStreamSynchronize(c->stream), "load sync");
     c->t = h.t;
     return LBM_OK;
 }
 
 extern "C" int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
-extern "C" int64_t lbm_fluid_count(const lbm_ctx* c) { return c ? c->n_cells - c->n_ghost : -1; }
+extern "C" int64_t lbm_fluid_count(const lbm_ctx* c) { return c ? c->n_store - c->n_ghost : -1; }
 extern "C" const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
 extern "C" void lbm_destroy(lbm_ctx* c) { delete c; }
 
@@ -578,9 +638,9 @@ namespace {
 
 struct AdjLayout {
     int nseg = 0, Kh = 0;  // segments; history slots H[1..Kh]
-    size_t sbytes = 0, wbytes = 0, rbytes = 0, lbytes = 0;
+    size_t sbytes = 0, wbytes = 0, lbytes = 0;
     size_t ck = 0, hist = 0, wck = 0, whist = 0, rck = 0, rhist = 0, lam[2] = {0, 0};
-    size_t mu = 0, region = 0, jpart = 0, bdelta = 0, bdphi = 0, count = 0, end = 0;
+    size_t mu = 0, gphi = 0, region = 0, jpart = 0, outs = 0, bdelta = 0, bdphi = 0, count = 0, end = 0;
 };
 
 AdjLayout adj_layout(const lbm_ctx* c, int T, int K)
@@ -589,27 +649,28 @@ AdjLayout adj_layout(const lbm_ctx* c, int T, int K)
     A.nseg = (T + K - 1) / K;
     A.Kh = K < T ? K : T;
     const size_t N = (size_t)c->N, Q = (size_t)c->grid.q;
-    const size_t n = (size_t)(c->n_cells > 0 ? c->n_cells : 1);
-    const size_t nb = (size_t)(c->n_cells - c->n_bulk > 0 ? c->n_cells - c->n_bulk : 1);
-    A.sbytes = align256(Q * N * elem_size(c->grid.storage));
+    const size_t n = (size_t)(c->n_store > 0 ? c->n_store : 1);
+    const size_t no = (size_t)(c->n_out > 0 ? c->n_out : 1);
+    A.sbytes = align256(Q * n * elem_size(c->grid.storage));
     A.wbytes = align256(n * 4);
-    A.rbytes = align256(N * 4);
-    A.lbytes = align256(Q * N * 4);
+    A.lbytes = align256(Q * n * 4);
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
     A.ck = take((size_t)A.nseg * A.sbytes);
     A.hist = take((size_t)A.Kh * A.sbytes);
     A.wck = take((size_t)A.nseg * A.wbytes);
     A.whist = take((size_t)A.Kh * A.wbytes);
-    A.rck = take((size_t)A.nseg * A.rbytes);
-    A.rhist = take((size_t)A.Kh * A.rbytes);
+    A.rck = take((size_t)A.nseg * A.wbytes);
+    A.rhist = take((size_t)A.Kh * A.wbytes);
     A.lam[0] = take(A.lbytes);
     A.lam[1] = take(A.lbytes);
     A.mu = take(n * 4);
+    A.gphi = take(n * 8);
     A.region = take(N);
     A.jpart = take((size_t)(total_blocks(c->base) + 1) * 8);
-    A.bdelta = take(Q * nb * 4);
-    A.bdphi = take(nb * 8);
+    A.outs = take(no * 4);
+    A.bdelta = take(Q * no * 4);
+    A.bdphi = take(no * 8);
     A.count = take(8);
     A.end = o;
     return A;
@@ -649,40 +710,45 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, const uint8_
     char* w = static_cast<char*>(workspace);
     const cudaStream_t st = c->stream;
     const size_t N = (size_t)c->N;
-    const size_t n = (size_t)c->n_cells;
+    const size_t n = (size_t)c->n_store;
     auto Cs = [&](int k) { return static_cast<void*>(w + AL.ck + (size_t)k * AL.sbytes); };
     auto Hs = [&](int j) { return static_cast<void*>(w + AL.hist + (size_t)(j - 1) * AL.sbytes); };
     auto Wc = [&](int k) { return reinterpret_cast<float*>(w + AL.wck + (size_t)k * AL.wbytes); };
     auto Wh = [&](int j) { return reinterpret_cast<float*>(w + AL.whist + (size_t)(j - 1) * AL.wbytes); };
-    auto Rc = [&](int k) { return reinterpret_cast<float*>(w + AL.rck + (size_t)k * AL.rbytes); };
-    auto Rh = [&](int j) { return reinterpret_cast<float*>(w + AL.rhist + (size_t)(j - 1) * AL.rbytes); };
+    auto Rc = [&](int k) { return reinterpret_cast<float*>(w + AL.rck + (size_t)k * AL.wbytes); };
+    auto Rh = [&](int j) { return reinterpret_cast<float*>(w + AL.rhist + (size_t)(j - 1) * AL.wbytes); };
     float* lam[2] = {reinterpret_cast<float*>(w + AL.lam[0]), reinterpret_cast<float*>(w + AL.lam[1])};
     float* mu = reinterpret_cast<float*>(w + AL.mu);
+    double* gphi = reinterpret_cast<double*>(w + AL.gphi);
     uint8_t* reg = reinterpret_cast<uint8_t*>(w + AL.region);
     double* jpart = reinterpret_cast<double*>(w + AL.jpart);
-    const uint32_t* cells = c->base.cells;
+    uint32_t* outs = reinterpret_cast<uint32_t*>(w + AL.outs);
+    const Params B = c->base;
 
     LBM_CUDA(cudaMemcpyAsync(reg, region, N, region_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
              "copy region");
+    if (c->n_out > 0)
+        LBM_CUDA(cudaMemcpyAsync(outs, c->out_slots.data(), (size_t)c->n_out * 4, cudaMemcpyHostToDevice, st),
+                 "copy outlet slots");
     unsigned long long* cnt_dev = reinterpret_cast<unsigned long long*>(w + AL.count);
     unsigned long long cnt = 0;
-    LBM_CUDA(launch_region_count(cells, c->n_cells, reg, cnt_dev, st), "region count");
+    LBM_CUDA(launch_region_count(B.rows, B.rowbase, B.mask, c->n_store, c->grid.nx, reg, cnt_dev, st), "region count");
     LBM_CUDA(cudaMemcpyAsync(&cnt, cnt_dev, sizeof(cnt), cudaMemcpyDeviceToHost, st), "copy region count");
     LBM_CUDA(cudaStreamSynchronize(st), "region count sync");
     if (cnt == 0) return fail(c, LBM_EINVAL, "the objective region holds no fluid cell");
-    const int nblk = total_blocks(c->base);
+    const int nblk = total_blocks(B);
     LBM_CUDA(cudaMemsetAsync(grad, 0, N * 8, st), "clear gradient");
+    LBM_CUDA(cudaMemsetAsync(gphi, 0, n * 8, st), "clear packed gradient");
     LBM_CUDA(cudaMemsetAsync(Cs(0), 0, AL.sbytes, st), "rest state");
     LBM_CUDA(cudaMemsetAsync(jpart, 0, (size_t)(nblk + 1) * 8, st), "clear objective partials");
     LBM_CUDA(launch_fill_f32(Wc(0), (long long)n, c->omega0, st), "initial omega");
 
-    const Params B = c->base;
-    auto step = [&](long long t, const void* src, void* dst, float* om, float* rho) {
+    auto step = [&](long long t, const void* src, void* dst, float* om, float* drho) {
         Params P = B;
         P.fsrc = src;
         P.fdst = dst;
         P.omega = om;
-        P.o_drho = rho;
+        P.o_drho = drho;
         P.t = t;
         return launch(c->grid, kModeStep, P, st);
     };
@@ -722,9 +788,11 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, const uint8_
     AdjParams A{};
     A.F = B;
     A.mu = mu;
-    A.gphi = grad;
+    A.gphi = gphi;
     A.region = reg;
     A.kappa = (float)(1.0 / ((double)T * (double)cnt));
+    A.out_slots = outs;
+    A.n_out = c->n_out;
     A.bnd_delta = reinterpret_cast<float*>(w + AL.bdelta);
     A.bnd_dphi = reinterpret_cast<double*>(w + AL.bdphi);
     A.jpart = jpart;
@@ -762,6 +830,7 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, const uint8_
         if (k == kl) LBM_CUDA(reverse(T, 1), "adjoint objective step");
         for (int t = e - 1; t >= s; --t) LBM_CUDA(reverse(t, 0), "adjoint reverse step");
     }
+    LBM_CUDA(launch_scatter_f64(B.rows, B.rowbase, B.mask, c->n_store, c->grid.nx, gphi, grad, st), "gradient scatter");
     std::vector<double> hp((size_t)nblk + 1, 0.0);
     if (nblk > 0)
         LBM_CUDA(cudaMemcpyAsync(hp.data(), jpart, (size_t)nblk * 8, cudaMemcpyDeviceToHost, st), "copy objective");
@@ -797,9 +866,9 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, const uint8_
 
 namespace {
 
-constexpr long long kNoAllocMaxCells = 8LL * 1024 * 1024;  // non-solid cells
-constexpr long long kNoAllocMaxBlocks = kNoAllocMaxCells / kBlock;
-// the step kernel's block split (fast + general ranges) may use one block more
+constexpr long long kNoAllocMaxCells = 8LL * 1024 * 1024;  // slots of the packed layout
+// lean blocks for kNoAllocMaxCells slots plus up to 32768 blocks of general-path cells
+constexpr long long kNoAllocMaxBlocks = kNoAllocMaxCells / kBlock + 32768;
 constexpr size_t kNoAllocSlots = (size_t)(kNoAllocMaxBlocks + 1) * kDiagSlots + 8;  // partials + result
 constexpr int kMaxDevices = 64;
 
@@ -828,9 +897,9 @@ extern "C" lbm_status lbm_diag_noalloc(lbm_ctx* c, const uint8_t* region, double
 {
     if (!c || !out) return LBM_EINVAL;
     if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
-    if (c->n_cells > kNoAllocMaxCells)
+    if (c->n_store > kNoAllocMaxCells)
         return fail(c, LBM_EINVAL, "lbm_diag_noalloc handles at most " + std::to_string(kNoAllocMaxCells) +
-                                       " non-solid cells, this context has " + std::to_string(c->n_cells) +
+                                       " packed cells, this context has " + std::to_string(c->n_store) +
                                        "; use lbm_diag");
     cudaPointerAttributes attr{};
     LBM_CUDA(cudaPointerGetAttributes(&attr, c->ws), "workspace attributes");
@@ -845,10 +914,13 @@ extern "C" lbm_status lbm_diag_noalloc(lbm_ctx* c, const uint8_t* region, double
         if (ra.type != cudaMemoryTypeDevice && ra.type != cudaMemoryTypeManaged)
             return fail(c, LBM_EINVAL, "lbm_diag_noalloc needs the region in device memory (or NULL)");
     }
-    if (c->n_cells == 0) {
+    if (c->n_store == 0) {
         for (int k = 0; k < 8; ++k) out[k] = 0.0;
         return LBM_OK;
     }
+    if (total_blocks(c->base) > kNoAllocMaxBlocks + 1)
+        return fail(c, LBM_EINVAL, "lbm_diag_noalloc handles at most " + std::to_string(32768 * 32) +
+                                       " general-path cells; use lbm_diag");
     double* scratch = nullptr;
     LBM_CUDA(noalloc_scratch(dev, &scratch), "cudaGetSymbolAddress of the diagnostics scratch");
     double* partials = scratch;

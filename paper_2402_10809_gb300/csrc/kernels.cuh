@@ -2,14 +2,17 @@
 // method with Carreau-Yasuda rheology (Horvat et al., arXiv 2402.10809,
 // Sec. 2-4), plus the moments and diagnostics epilogues that reuse its pull.
 //
-// One thread owns one non-solid cell taken from a compact cell list, so no
-// thread idles on the solid voxels of a sparse aneurysm box.  The list is
-// ordered [plain bulk cells][bulk cells on a periodic face][inlet][outlet];
-// blocks covering the first part run the lean path (kernel-uniform neighbour
-// offsets, no boundary code), blocks covering the rest run the general path.
-// The distributions live in two dense SoA buffers f[i][N]; a warp of
-// consecutive list entries reads and writes consecutive addresses of each
-// direction plane.
+// Row-packed layout.  Each x-row (y, z) of the box stores only the span
+// [xmin, xmax] of its non-solid cells, and the spans of all rows are packed
+// back to back: the slot of (x, y, z) is rowbase[y + ny z] + x.  One thread
+// owns one slot, so no thread idles on the solid voxels of a sparse aneurysm
+// box, and the few solid cells inside a span (gaps between vessel and sac) are
+// ghost slots.  A warp of consecutive slots reads and writes consecutive
+// addresses of each direction plane, also across the ends of rows, because
+// the source of every pull lies in a packed span too.  The distributions live
+// in two SoA buffers f[i][n_store].  Cells off periodic faces and off the
+// open boundaries take the lean path (source slots from one per-row record of
+// the nine neighbour-row bases); the others call the general path.
 //
 // Stored values are deviations g_i = f_i - w_i phi_hat_i, where phi_hat_i is
 // the porosity of the cell the value streams to (own porosity across solid or
@@ -26,13 +29,17 @@
 
 namespace lbm {
 
-// Per-cell mask word: bit i (i < Q) set when direction i cannot be pulled from
+// Per-slot mask word: bit i (i < Q) set when direction i cannot be pulled from
 // its source y - c_i (solid, box wall, or an open face); bits 27-28 cell type;
 // bit 29 set when some fluid neighbour has a different porosity; bit 30 set
-// when a neighbour lies across a periodic face.
+// when the cell lies on a periodic face; bit 31 marks a ghost slot (a solid
+// cell inside a packed span), whose bit 0 asks for zero stores (it shares an
+// aligned 8-slot group with a fluid slot).
 constexpr uint32_t kTypeShift = 27;
 constexpr uint32_t kPorousBit = 1u << 29;
 constexpr uint32_t kWrapBit = 1u << 30;
+constexpr uint32_t kGhostBit = 1u << 31;
+constexpr uint32_t kGeneralBits = (3u << kTypeShift) | kWrapBit;
 enum { kBulk = 0, kInlet = 1, kOutlet = 2 };
 enum { kModeStep = 0, kModeMoments = 1, kModeDiag = 2 };
 constexpr int kBlock = 256;
@@ -45,13 +52,21 @@ constexpr int kDiagSlots = 9;
 struct Params {
     // geometry
     int nx, ny, nz;
-    long long N;
-    int n_cells, n_fast, n_bulk;
-    const uint32_t* cells;    // dense index of each listed cell
-    const uint32_t* mask;     // list order
-    const float* phi;         // dense porosity
-    const float* bnd_prof;    // [n_cells - n_bulk]: inlet profile 2 max(0, 1 - r^2/R^2)
-    const uint32_t* bnd_nbmask;  // [n_cells - n_bulk]: mask of the outlet's interior neighbour
+    long long N;              // box cells (dense outputs)
+    int n_store;              // slots of the packed layout
+    int wide;                 // Q n_store >= 2^32: every cell takes the general path (64-bit offsets)
+    int n_general;            // cells of the general path (periodic faces, inlet, outlet; all when wide)
+    int gen_block;            // general cells per block (32 or kBlock)
+    const uint32_t* general;  // [n_general] their slots, ascending
+    const uint32_t* rows;     // [n_store] row y + ny z of each slot
+    const int4* rownb;        // [ny nz][3] per row: bases of the neighbour rows (y + sy, z + sz)
+                              // (wrapped on periodic axes) at index (sy + 1) + 3 (sz + 1),
+                              // then y, z, 0, 0
+    const int* rowbase;       // [ny nz] slot of (x, row) = rowbase[row] + x
+    const uint32_t* mask;     // [n_store]
+    const float* phi;         // [n_store] porosity
+    const float* bnd_prof;    // [n_store] inlet cells: profile 2 max(0, 1 - r^2/R^2)
+    const uint32_t* bnd_nbmask;  // [n_store] outlet cells: mask of the interior neighbour
     // physics, lattice units
     float gx, gy, gz;         // body force per unit mass
     int drag_kc;              // 1 Kozeny-Carman, 0 constant permeability
@@ -65,24 +80,30 @@ struct Params {
     // state
     const void* fsrc;
     void* fdst;
-    float* omega;             // list order; omega(t-1) in, omega(t) out
+    float* omega;             // [n_store] omega(t-1) in, omega(t) out
     long long t;
-    // moments outputs (dense or list order, any may be null)
+    // moments outputs (dense or slot order, any may be null)
     float *o_rho, *o_ux, *o_uy, *o_uz, *o_gdot, *o_omega;
     int o_compact;
-    float* o_drho;            // time step: rho - 1 of time t (dense, may be null)
+    float* o_drho;            // time step: rho - 1 of time t per slot (may be null)
     // diagnostics
     const uint8_t* region;    // dense, may be null
     double* partials;         // [gridDim.x][kDiagSlots]
 };
 
-// Blocks of the launch: the general-path cells [n_fast, n_cells) first, so
-// that their slower blocks overlap the bulk instead of trailing it, then the
-// fast cells [0, n_fast).
-__host__ __device__ inline int general_blocks(const Params& P) { return (P.n_cells - P.n_fast + kBlock - 1) / kBlock; }
+// Blocks of a launch: first the general-path cells, gen_block per block, then
+// one thread per slot for the lean path, which skips ghost and general slots.
+// Leading the grid lets the slower general blocks overlap the bulk.  Their
+// cells lie in different rows, so their loads do not coalesce: on small grids
+// the host asks for one warp's worth per block (gen_block = 32) to spread them
+// over many SMs; on large grids full blocks keep the block slots for the bulk.
+__host__ __device__ inline int general_blocks(const Params& P)
+{
+    return (P.n_general + P.gen_block - 1) / P.gen_block;
+}
 __host__ __device__ inline int total_blocks(const Params& P)
 {
-    return general_blocks(P) + (P.n_fast + kBlock - 1) / kBlock;
+    return general_blocks(P) + (P.n_store + kBlock - 1) / kBlock;
 }
 
 // ------------------------------------------------------------------ storage
@@ -249,64 +270,94 @@ __device__ __forceinline__ Moments<Q> moments(const float* g)
 
 // ------------------------------------------------------------------ helpers
 
+// Bases of the nine neighbour rows of a cell, index (sy + 1) + 3 (sz + 1) for the
+// row (y + sy, z + sz), wrapped on periodic axes.
+struct RowBases {
+    int b[9];
+};
+
+__device__ __forceinline__ RowBases row_bases(const Params& P, uint32_t r)
+{
+    const int4* rn = P.rownb + 3 * (size_t)r;
+    const int4 a = __ldg(rn), c = __ldg(rn + 1), d = __ldg(rn + 2);
+    RowBases R;
+    R.b[0] = a.x; R.b[1] = a.y; R.b[2] = a.z; R.b[3] = a.w;
+    R.b[4] = c.x; R.b[5] = c.y; R.b[6] = c.z; R.b[7] = c.w;
+    R.b[8] = d.x;
+    return R;
+}
+
+// A cell of the general path: its coordinates, slot and dense index, the
+// wrapped neighbour x and the bases of its neighbour rows.
 struct Coords {
     int x, y, z;
-    long long idx;
+    long long slot;  // packed slot
+    long long idx;   // dense index x + nx (y + ny z)
     int X[3];        // x - 1, x, x + 1 (wrapped)
-    long long Y[3];  // (y - 1, y, y + 1) * nx (wrapped)
-    long long Z[3];  // (z - 1, z, z + 1) * nx * ny (wrapped)
+    RowBases rb;
 };
 
 __device__ __forceinline__ Coords make_coords(const Params& P, int x, int y, int z)
 {
     Coords c;
     c.x = x; c.y = y; c.z = z;
-    long long sy = P.nx, sz = (long long)P.nx * P.ny;
-    c.idx = x + sy * y + sz * z;
+    c.idx = x + (long long)P.nx * (y + (long long)P.ny * z);
+    c.rb = row_bases(P, (uint32_t)(y + P.ny * z));
+    c.slot = (long long)c.rb.b[4] + x;
     c.X[0] = x == 0 ? P.nx - 1 : x - 1;
     c.X[1] = x;
     c.X[2] = x == P.nx - 1 ? 0 : x + 1;
-    c.Y[0] = sy * (y == 0 ? P.ny - 1 : y - 1);
-    c.Y[1] = sy * y;
-    c.Y[2] = sy * (y == P.ny - 1 ? 0 : y + 1);
-    c.Z[0] = sz * (z == 0 ? P.nz - 1 : z - 1);
-    c.Z[1] = sz * z;
-    c.Z[2] = sz * (z == P.nz - 1 ? 0 : z + 1);
     return c;
 }
 
-__device__ __forceinline__ Coords coords_of(const Params& P, uint32_t idx)
+// Coordinates of slot p (row from the slot's row id, x from the row base).
+__device__ __forceinline__ Coords coords_of(const Params& P, int p)
 {
-    const uint32_t plane = (uint32_t)P.nx * (uint32_t)P.ny;
-    const uint32_t z = idx / plane;
-    const uint32_t r = idx - z * plane;
-    const uint32_t y = r / (uint32_t)P.nx;
-    return make_coords(P, (int)(r - y * (uint32_t)P.nx), (int)y, (int)z);
+    const uint32_t r = P.rows[p];
+    Coords c;
+    c.rb = row_bases(P, r);
+    const int4 yz = __ldg(P.rownb + 3 * (size_t)r + 2);
+    c.y = yz.y;
+    c.z = yz.z;
+    c.x = p - c.rb.b[4];
+    c.slot = p;
+    c.idx = c.x + (long long)P.nx * r;
+    c.X[0] = c.x == 0 ? P.nx - 1 : c.x - 1;
+    c.X[1] = c.x;
+    c.X[2] = c.x == P.nx - 1 ? 0 : c.x + 1;
+    return c;
 }
 
-// Dense index of y + (dx, dy, dz) with periodic wrap (dx etc. in {-1, 0, 1}).
-__device__ __forceinline__ long long shifted(const Coords& c, int dx, int dy, int dz)
+// Slot of y + (dx, dy, dz) with periodic wrap (dx etc. in {-1, 0, 1}); only
+// meaningful where that cell is non-solid.
+__device__ __forceinline__ long long shifted(const Params& P, const Coords& c, int dx, int dy, int dz)
 {
-    return c.X[dx + 1] + c.Y[dy + 1] + c.Z[dz + 1];
+    return (long long)c.rb.b[(dy + 1) + 3 * (dz + 1)] + c.X[dx + 1];
 }
 
-
-// Source (plane, index) of direction i: g_i = f*_i(y - c_i), or the cell's own
+// Source (plane, slot) of direction i: g_i = f*_i(y - c_i), or the cell's own
 // f*_opp(i) (half-way bounce-back, Sec. 4) where the source is not available.
 template <int Q>
-__device__ __forceinline__ long long pull_offset(long long N, const Coords& c, uint32_t mask, int i)
+__device__ __forceinline__ long long pull_offset(const Params& P, const Coords& c, uint32_t mask, int i)
 {
     using L = Lattice<Q>;
-    return ((mask >> i) & 1u) ? (long long)opp(i) * N + c.idx
-                              : (long long)i * N + shifted(c, -L::cx(i), -L::cy(i), -L::cz(i));
+    const long long n = P.n_store;
+    return ((mask >> i) & 1u) ? (long long)opp(i) * n + c.slot
+                              : (long long)i * n + shifted(P, c, -L::cx(i), -L::cy(i), -L::cz(i));
 }
 
 template <int Q, class T>
-__device__ __forceinline__ void pull_general(const T* __restrict__ f, long long N, const Coords& c, uint32_t mask,
-                                             float* g)
+__device__ __forceinline__ void pull_general(const Params& P, const T* __restrict__ f, const Coords& c,
+                                             uint32_t mask, float* g)
 {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = Store<T>::ld(f + pull_offset<Q>(N, c, mask, i));
+    for (int i = 0; i < Q; ++i) g[i] = Store<T>::ld(f + pull_offset<Q>(P, c, mask, i));
+}
+
+// Lean-path slot of (x + dx, y + dy, z + dz) in 32-bit arithmetic.
+__device__ __forceinline__ uint32_t lean_slot(const RowBases& R, int x, int dx, int dy, int dz)
+{
+    return (uint32_t)(R.b[(dy + 1) + 3 * (dz + 1)] + x + dx);
 }
 
 // Mean inflow v(t) = u0 (1 + amp sin(2 pi t / period)), linear ramp over the
@@ -384,12 +435,12 @@ __device__ __forceinline__ void outlet(const Params& P, const Coords& c, float p
     const int ax = P.out_axis;
     const int sgn = P.out_side == 1 ? -1 : 1;
     const Coords nc = make_coords(P, c.x + (ax == 0 ? sgn : 0), c.y + (ax == 1 ? sgn : 0), c.z + (ax == 2 ? sgn : 0));
-    const float phin = __ldg(P.phi + nc.idx);
+    const float phin = __ldg(P.phi + nc.slot);
     const T* f = static_cast<const T*>(P.fsrc);
     float sd = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const float v = Store<T>::ld(f + pull_offset<Q>(P.N, nc, nbmask, i));
+        const float v = Store<T>::ld(f + pull_offset<Q>(P, nc, nbmask, i));
         sd += v;
         if (L::cx(i)) mx += L::cx(i) > 0 ? v : -v;
         if (L::cy(i)) my += L::cy(i) > 0 ? v : -v;
@@ -400,7 +451,7 @@ __device__ __forceinline__ void outlet(const Params& P, const Coords& c, float p
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (c_axis<Q>(i, ax) * sgn > 0) {
-            const float gn = Store<T>::ld(f + pull_offset<Q>(P.N, nc, nbmask, i));
+            const float gn = Store<T>::ld(f + pull_offset<Q>(P, nc, nbmask, i));
             const float cu = cdot(L::cx(i), L::cy(i), L::cz(i), M.ux, M.uy, M.uz);
             const float pe = 3.0f * cu + 4.5f * cu * cu - 1.5f * uu;
             // (f^eq(rho_out) - w phi) + (g_nb + w phi_nb) - f^eq(rho_nb)
@@ -444,52 +495,44 @@ __device__ __forceinline__ void block_reduce_diag(double* v, double* partials)
 
 // ------------------------------------------------------------------ the kernel
 
+// One cell of the fused step / moments / diagnostics: slot p with its link
+// mask, lean or general path; diagnostics accumulate into dv.
 // MODE kModeStep: full time step (pull, boundaries, moments, relaxation rate,
 // collision, store).  kModeMoments: pull + boundaries + moments and fields of
 // the current time.  kModeDiag: the same fields reduced to diagnostics.
-// One cell of the fused step / moments / diagnostics: list position p, its
-// dense index idx and link mask, fast or general path; diagnostics accumulate
-// into dv.
 // park: this thread's column of a Q x kBlock shared array (time step only).
 template <int Q, class T, int MODE, bool fast>
-__device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t idx, uint32_t mask, double* dv,
-                                          volatile float* park)
+__device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t mask, double* dv, volatile float* park)
 {
     using L = Lattice<Q>;
-    if (fast && (idx & 0x80000000u)) {
-        // ghost entry (a solid cell sharing a 16-cell group with bulk cells):
-        // complete this cell's sectors with zeros; nothing reads them.
-        if (MODE == kModeStep) {
-            T* __restrict__ gd = static_cast<T*>(P.fdst) + (idx & 0x7fffffffu);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) Store<T>::st(gd + (size_t)i * P.N, 0.0f);
-        }
-        return;
-    }
-    const float phi = __ldg(P.phi + idx);
+    const float phi = __ldg(P.phi + p);
     const T* __restrict__ fs = static_cast<const T*>(P.fsrc);
-    const uint32_t N = (uint32_t)P.N;
-    const int sy = P.nx, sz = P.nx * P.ny;
+    const uint32_t n = (uint32_t)P.n_store;
     float g[Q];
-    Coords cg;  // general path: wrapped neighbour coordinates of this cell
+    Coords cg;     // general path: wrapped neighbour coordinates of this cell
+    RowBases rb;   // lean path: bases of the nine neighbour rows
+    int x = 0;
+    uint32_t row = 0;
     if (fast) {
-        // y - c_i never wraps here: index = idx - (c_x + c_y nx + c_z nx ny);
-        // element offsets fit 32 bits (the host routes larger boxes to the
-        // general path).
+        // y - c_i never wraps here and every offset fits 32 bits (the host
+        // sends larger layouts down the general path).
+        row = P.rows[p];
+        rb = row_bases(P, row);
+        x = p - rb.b[4];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const uint32_t d = (uint32_t)(L::cx(i) + L::cy(i) * sy + L::cz(i) * sz);
-            const uint32_t o = ((mask >> i) & 1u) ? (uint32_t)opp(i) * N + idx : (uint32_t)i * N + idx - d;
+            const uint32_t o = ((mask >> i) & 1u) ? (uint32_t)opp(i) * n + (uint32_t)p
+                                                  : (uint32_t)i * n + lean_slot(rb, x, -L::cx(i), -L::cy(i), -L::cz(i));
             g[i] = Store<T>::ld(fs + o);
         }
     } else {
-        cg = coords_of(P, idx);
-        pull_general<Q, T>(fs, P.N, cg, mask, g);
+        cg = coords_of(P, p);
+        pull_general<Q, T>(P, fs, cg, mask, g);
         const int type = (mask >> kTypeShift) & 3u;
         if (type == kInlet) {
-            zou_he<Q>(P, P.bnd_prof[p - P.n_bulk], g);
+            zou_he<Q>(P, P.bnd_prof[p], g);
         } else if (type == kOutlet) {
-            outlet<Q, T>(P, cg, phi, P.bnd_nbmask[p - P.n_bulk], g);
+            outlet<Q, T>(P, cg, phi, P.bnd_nbmask[p], g);
         }
     }
     // The time step parks the pulled populations in this thread's column of
@@ -530,7 +573,7 @@ __device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t idx, 
         const float gk = 9.0f * h;
         const float os = 3.0f * om * M.sigma;
         const float of = 3.0f * h;
-        T* __restrict__ dp = fd + idx;  // this cell in plane 0; plane i at + i N
+        T* __restrict__ dp = fd + p;  // this cell in plane 0; plane i at + i n_store
         {
             const float w = L::w(0);
             Store<T>::st(dp, fmaf(omo, park[0], w * e0));
@@ -553,26 +596,26 @@ __device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t idx, 
                 // (the stored reference moves to phi(y + c_i)): w (rho - 1) dphi.
                 // A set mask bit means that neighbour is solid or outside: the
                 // cell reads its own porosity there, so dphi = 0 without a branch.
-                const uint32_t d = (uint32_t)(cx + cy * sy + cz * sz);
                 const float wd = w * M.drho;
                 uint32_t ni, nj;
                 if (fast) {
-                    ni = ((mask >> j) & 1u) ? idx : idx + d;
-                    nj = ((mask >> i) & 1u) ? idx : idx - d;
+                    ni = ((mask >> j) & 1u) ? (uint32_t)p : lean_slot(rb, x, cx, cy, cz);
+                    nj = ((mask >> i) & 1u) ? (uint32_t)p : lean_slot(rb, x, -cx, -cy, -cz);
                 } else {
-                    ni = ((mask >> j) & 1u) ? idx : (uint32_t)shifted(cg, cx, cy, cz);
-                    nj = ((mask >> i) & 1u) ? idx : (uint32_t)shifted(cg, -cx, -cy, -cz);
+                    ni = ((mask >> j) & 1u) ? (uint32_t)p : (uint32_t)shifted(P, cg, cx, cy, cz);
+                    nj = ((mask >> i) & 1u) ? (uint32_t)p : (uint32_t)shifted(P, cg, -cx, -cy, -cz);
                 }
                 vi = fmaf(wd, __ldg(P.phi + ni) - phi, vi);
                 vj = fmaf(wd, __ldg(P.phi + nj) - phi, vj);
             }
-            Store<T>::st(dp + (size_t)i * P.N, vi);
-            Store<T>::st(dp + (size_t)j * P.N, vj);
+            Store<T>::st(dp + (size_t)i * n, vi);
+            Store<T>::st(dp + (size_t)j * n, vj);
         }
         P.omega[p] = om;
-        if (P.o_drho) P.o_drho[idx] = M.drho;  // density deviation of time t (adjoint replay)
+        if (P.o_drho) P.o_drho[p] = M.drho;  // density deviation of time t (adjoint replay)
     } else if (MODE == kModeMoments) {
-        const long long o = P.o_compact ? (long long)p : (long long)idx;
+        const long long idx = fast ? (long long)x + (long long)P.nx * row : cg.idx;
+        const long long o = P.o_compact ? (long long)p : idx;
         if (P.o_rho) P.o_rho[o] = M.rho;
         if (P.o_ux) P.o_ux[o] = M.ux;
         if (P.o_uy) P.o_uy[o] = M.uy;
@@ -587,6 +630,7 @@ __device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t idx, 
             dv[0] = phi;
             dv[1] = M.sd;
             dv[2] = 0.5 * (double)M.rho * (double)un * (double)un;
+            const long long idx = fast ? (long long)x + (long long)P.nx * row : cg.idx;
             if (P.region && P.region[idx]) {
                 dv[3] = un;
                 dv[4] = 1.0;
@@ -599,22 +643,34 @@ __device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t idx, 
 }
 
 // Cells of the general path (periodic wrap, inlet, outlet) in a function of
-// their own, so that their register needs do not bound the fast path.
+// their own, so that their register needs do not bound the lean path.
 template <int Q, class T, int MODE>
-__device__ __noinline__ void cell_general(const Params& P, int p, uint32_t idx, uint32_t mask, double* dv,
-                                          volatile float* park)
+__device__ __noinline__ void cell_general(const Params& P, int p, uint32_t mask, double* dv, volatile float* park)
 {
-    cell_impl<Q, T, MODE, false>(P, p, idx, mask, dv, park);
+    cell_impl<Q, T, MODE, false>(P, p, mask, dv, park);
 }
 
+// A ghost slot: complete its sectors with zeros where it shares an aligned
+// 8-slot group with fluid slots (nothing ever reads it).
 template <int Q, class T, int MODE>
-__device__ __forceinline__ void cell_body(const Params& P, int p, uint32_t idx, uint32_t mask, bool fast, double* dv,
-                                          volatile float* park)
+__device__ __forceinline__ void ghost_slot(const Params& P, int p, uint32_t mask)
 {
-    if (fast)
-        cell_impl<Q, T, MODE, true>(P, p, idx, mask, dv, park);
-    else
-        cell_general<Q, T, MODE>(P, p, idx, mask, dv, park);
+    if (MODE == kModeStep && (mask & 1u)) {
+        T* __restrict__ gd = static_cast<T*>(P.fdst) + p;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Store<T>::st(gd + (size_t)i * P.n_store, 0.0f);
+    }
+}
+
+// Lean-path thread of slot p: ghost slots store zeros where needed, general
+// cells are left to the general blocks.
+template <int Q, class T, int MODE>
+__device__ __forceinline__ void lean_body(const Params& P, int p, uint32_t mask, double* dv, volatile float* park)
+{
+    if (mask & kGhostBit)
+        ghost_slot<Q, T, MODE>(P, p, mask);
+    else if (!(mask & kGeneralBits) && !P.wide)
+        cell_impl<Q, T, MODE, true>(P, p, mask, dv, park);
 }
 
 // Shared column for parking the pulled populations during a time step.
@@ -633,15 +689,20 @@ template <int Q, class T, int MODE>
 __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS) lbm_kernel(const Params P)
 {
     const int nbg = general_blocks(P);
-    const bool fast = (int)blockIdx.x >= nbg;
-    const int p = fast ? ((int)blockIdx.x - nbg) * kBlock + (int)threadIdx.x
-                       : P.n_fast + (int)blockIdx.x * kBlock + (int)threadIdx.x;
-    const int pend = fast ? P.n_fast : P.n_cells;
     double dv[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1e300, -1e300, 0.0};
     // dv: 0 sum phi, 1 sum (phi rho - phi), 2 kinetic energy, 3 region sum |u|,
     //     4 region count, 5 max |u|, 6 min omega, 7 max omega, 8 non-finite count
     volatile float* park = park_column<Q, MODE>();
-    if (p < pend) cell_body<Q, T, MODE>(P, p, P.cells[p], P.mask[p], fast, dv, park);
+    if ((int)blockIdx.x < nbg) {
+        const int k = (int)blockIdx.x * P.gen_block + (int)threadIdx.x;
+        if ((int)threadIdx.x < P.gen_block && k < P.n_general) {
+            const int p = (int)P.general[k];
+            cell_general<Q, T, MODE>(P, p, P.mask[p], dv, park);
+        }
+    } else {
+        const int p = ((int)blockIdx.x - nbg) * kBlock + (int)threadIdx.x;
+        if (p < P.n_store) lean_body<Q, T, MODE>(P, p, P.mask[p], dv, park);
+    }
     if (MODE == kModeDiag) block_reduce_diag(dv, P.partials);
 }
 

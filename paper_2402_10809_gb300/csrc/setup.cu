@@ -1,10 +1,7 @@
-// Set-up kernels: the compact cell list, the per-cell link masks and boundary
-// data, the initial state, checkpoints and the final diagnostics reduction.
-//
-// The cell list is built by a deterministic three-pass compaction (count per
-// chunk, single-block scan, emit), ordered as bulk fluid cells by dense index,
-// then inlet cells, then outlet cells, so that boundary cells fill their own
-// warps at the end of the step launch.
+// Set-up kernels: the row spans of the packed layout, the per-slot row ids,
+// porosity, link masks and boundary data, small utility kernels and the final
+// diagnostics reduction.  The spans are scanned on the host (their count is
+// the number of rows), so the layout is deterministic.
 #include <stdint.h>
 
 #include "kernels.cuh"
@@ -12,145 +9,50 @@
 
 namespace lbm {
 
-__device__ __forceinline__ bool on_periodic_face(long long idx, const CellGrid& G)
-{
-    const long long plane = (long long)G.nx * G.ny;
-    const int z = (int)(idx / plane);
-    const long long r = idx - (long long)z * plane;
-    const int y = (int)(r / G.nx);
-    const int x = (int)(r - (long long)y * G.nx);
-    return (G.periodic[0] && (x == 0 || x == G.nx - 1)) || (G.periodic[1] && (y == 0 || y == G.ny - 1)) ||
-           (G.periodic[2] && (z == 0 || z == G.nz - 1));
-}
+__device__ __forceinline__ bool fluid_flag(uint8_t f) { return f >= 1 && f <= 3; }
 
-// List group of a cell: 0 bulk off periodic faces (and ghosts, see setup.cuh),
-// 1 bulk on a periodic face, 2 inlet, 3 outlet, -1 not listed.
-__device__ __forceinline__ int category(uint8_t f, long long idx, const CellGrid& G, bool group_has_bulk)
+// One warp per row (y, z): the span [xmin, xmax] of its non-solid cells
+// (ext = 0 for a row without any); flags outside 0..3 raise kErrFlag.
+__global__ void setup_rows(const uint8_t* __restrict__ flags, int nx, int nrows, int* __restrict__ xmin,
+                           int* __restrict__ ext, uint32_t* __restrict__ err)
 {
-    if (f == 2) return 2;
-    if (f == 3) return 3;
-    if (f == 0) return group_has_bulk ? 0 : -1;
-    if (f != 1) return -1;
-    return on_periodic_face(idx, G) ? 1 : 0;
-}
-
-// Whether the ghost group of this thread's cells holds a bulk cell of group 0.
-__device__ __forceinline__ bool group_has_bulk(const uint8_t* flags, long long base, long long N, const CellGrid& G)
-{
-    for (int k = 0; k < kSetupCellsPerThread; ++k) {
-        const long long idx = base + k;
-        if (idx < N && flags[idx] == 1 && !on_periodic_face(idx, G)) return true;
-    }
-    return false;
-}
-
-// Inclusive scan over a 256-thread block; returns the exclusive prefix and the
-// block total.
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total)
-{
-    __shared__ uint32_t warp_tot[kSetupThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
-        if (lane >= off) x += y;
-    }
-    if (lane == 31) warp_tot[wid] = x;
-    __syncthreads();
-    uint32_t base = 0, tot = 0;
-    for (int w = 0; w < kSetupThreads / 32; ++w) {
-        if (w < wid) base += warp_tot[w];
-        tot += warp_tot[w];
-    }
-    __syncthreads();
-    *total = tot;
-    return base + x - v;
-}
-
-__global__ void setup_count(const uint8_t* __restrict__ flags, long long N, CellGrid G, int nblk,
-                            uint32_t* __restrict__ counts)
-{
-    const long long base = (long long)blockIdx.x * kSetupChunk + (long long)threadIdx.x * kSetupCellsPerThread;
-    const bool gb = group_has_bulk(flags, base, N, G);
-    uint32_t c[kCounters] = {0, 0, 0, 0, 0};
-    for (int k = 0; k < kSetupCellsPerThread; ++k) {
-        const long long idx = base + k;
-        if (idx < N) {
-            const int cat = category(flags[idx], idx, G, gb);
-            if (cat >= 0) c[cat] += 1;
-            if (cat == 0 && flags[idx] == 0) c[kCategories] += 1;
+    const int r = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= nrows) return;
+    const uint8_t* row = flags + (size_t)r * nx;
+    int lo = nx, hi = -1;
+    bool bad = false;
+    for (int x0 = 0; x0 < nx; x0 += 32) {
+        const int x = x0 + lane;
+        const uint8_t f = x < nx ? row[x] : 0;
+        bad |= f > 3;
+        const uint32_t b = __ballot_sync(0xffffffffu, fluid_flag(f));
+        if (b) {
+            lo = min(lo, x0 + __ffs(b) - 1);
+            hi = max(hi, x0 + 31 - __clz(b));
         }
     }
-    for (int cat = 0; cat < kCounters; ++cat) {
-        uint32_t tot;
-        block_exclusive_scan(c[cat], &tot);
-        if (threadIdx.x == 0) counts[cat * nblk + blockIdx.x] = tot;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, kErrFlag);
+    if (lane == 0) {
+        xmin[r] = hi >= 0 ? lo : 0;
+        ext[r] = hi >= 0 ? hi - lo + 1 : 0;
     }
 }
 
-// One block: exclusive scan of counts[kCategories * nblk] (category-major) into
-// offsets, and the category totals.
-__global__ void setup_scan(const uint32_t* __restrict__ counts, int nblk, uint32_t* __restrict__ offsets,
-                           uint32_t* __restrict__ totals)
+// One warp per row: the row id of each slot of its span and the packed porosity.
+__global__ void setup_slots(const float* __restrict__ phi, int nx, int nrows, const int* __restrict__ rowbase,
+                            const int* __restrict__ xmin, const int* __restrict__ ext, uint32_t* __restrict__ rows,
+                            float* __restrict__ phi_s)
 {
-    __shared__ uint32_t part[1024];
-    const int n = kCategories * nblk;
-    const int per = (n + 1023) / 1024;
-    const int lo = threadIdx.x * per;
-    const int hi = min(n, lo + per);
-    uint32_t s = 0;
-    for (int k = lo; k < hi; ++k) s += counts[k];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int k = 0; k < 1024; ++k) {
-            uint32_t v = part[k];
-            part[k] = run;
-            run += v;
-        }
-    }
-    __syncthreads();
-    uint32_t run = part[threadIdx.x];
-    for (int k = lo; k < hi; ++k) {
-        offsets[k] = run;
-        run += counts[k];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int cat = 0; cat < kCounters; ++cat) {
-            uint32_t t = 0;
-            for (int b = 0; b < nblk; ++b) t += counts[cat * nblk + b];
-            totals[cat] = t;
-        }
-    }
-}
-
-__global__ void setup_emit(const uint8_t* __restrict__ flags, long long N, CellGrid G, int nblk,
-                           const uint32_t* __restrict__ offsets, uint32_t* __restrict__ cells)
-{
-    const long long base = (long long)blockIdx.x * kSetupChunk + (long long)threadIdx.x * kSetupCellsPerThread;
-    const bool gb = group_has_bulk(flags, base, N, G);
-    uint32_t c[kCategories] = {0, 0, 0, 0};
-    for (int k = 0; k < kSetupCellsPerThread; ++k) {
-        const long long idx = base + k;
-        if (idx < N) {
-            const int cat = category(flags[idx], idx, G, gb);
-            if (cat >= 0) c[cat] += 1;
-        }
-    }
-    uint32_t pos[kCategories];
-    for (int cat = 0; cat < kCategories; ++cat) {
-        uint32_t tot;
-        pos[cat] = offsets[cat * nblk + blockIdx.x] + block_exclusive_scan(c[cat], &tot);
-    }
-    for (int k = 0; k < kSetupCellsPerThread; ++k) {
-        const long long idx = base + k;
-        if (idx < N) {
-            const int cat = category(flags[idx], idx, G, gb);
-            if (cat >= 0) cells[pos[cat]++] = (uint32_t)idx | (flags[idx] == 0 ? kGhostFlag : 0u);
-        }
+    const int r = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= nrows) return;
+    const int e = ext[r];
+    const int x0 = xmin[r];
+    const long long s0 = (long long)rowbase[r] + x0;
+    for (int k = lane; k < e; k += 32) {
+        rows[s0 + k] = (uint32_t)r;
+        phi_s[s0 + k] = phi[(size_t)r * nx + x0 + k];
     }
 }
 
@@ -192,38 +94,54 @@ __device__ uint32_t link_mask(const SetupParams& S, int x, int y, int z, int typ
     for (int i = 0; i < Q; ++i) {
         long long s;
         int ax, sd;
-        if (!step_to(S, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i), &s, &ax, &sd) || S.flags[s] == 0) m |= 1u << i;
+        if (!step_to(S, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i), &s, &ax, &sd) || !fluid_flag(S.flags[s]))
+            m |= 1u << i;
     }
     for (int i = 1; i < Q; ++i) {
         long long d;
         int ax, sd;
-        if (step_to(S, x, y, z, L::cx(i), L::cy(i), L::cz(i), &d, &ax, &sd) && S.flags[d] != 0 && S.phi[d] != phi)
+        if (step_to(S, x, y, z, L::cx(i), L::cy(i), L::cz(i), &d, &ax, &sd) && fluid_flag(S.flags[d]) &&
+            S.phi[d] != phi)
             m |= kPorousBit;
     }
     return m;
+}
+
+// Dense index of slot q.
+__device__ __forceinline__ long long slot_dense(const SetupParams& S, int q)
+{
+    const uint32_t r = S.rows[q];
+    return (long long)(q - S.rowbase[r]) + (long long)S.nx * r;
 }
 
 template <int Q>
 __global__ void setup_mask(const SetupParams S)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= S.n_cells) return;
-    const uint32_t pc = S.cells[p];
-    if (pc & kGhostFlag) {
-        S.mask[p] = kGhostFlag;
+    if (p >= S.n_store) return;
+    const uint32_t r = S.rows[p];
+    const int x = p - S.rowbase[r];
+    const int y = (int)(r % (uint32_t)S.ny);
+    const int z = (int)(r / (uint32_t)S.ny);
+    const long long idx = x + (long long)S.nx * r;
+    const uint8_t fl = S.flags[idx];
+    if (!fluid_flag(fl)) {
+        // ghost slot: zero stores only where an aligned 8-slot group holds fluid
+        const int g0 = p & ~7;
+        bool store = false;
+        for (int q = g0; q < g0 + 8 && q < S.n_store; ++q) store |= fluid_flag(S.flags[slot_dense(S, q)]);
+        S.mask[p] = kGhostBit | (store ? 1u : 0u);
+        S.bnd_prof[p] = 0.0f;
+        S.bnd_nbmask[p] = 0u;
         return;
     }
-    const long long idx = pc;
-    const long long plane = (long long)S.nx * S.ny;
-    const int z = (int)(idx / plane);
-    const int y = (int)((idx - (long long)z * plane) / S.nx);
-    const int x = (int)(idx - (long long)z * plane - (long long)y * S.nx);
-    const uint8_t fl = S.flags[idx];
     const float phi = S.phi[idx];
     uint32_t err = 0;
     if (!(phi > 0.0f) || !(phi <= 1.0f)) err |= kErrPorosity;
     const int type = fl == 2 ? kInlet : fl == 3 ? kOutlet : kBulk;
     S.mask[p] = link_mask<Q>(S, x, y, z, type);
+    S.bnd_prof[p] = 0.0f;
+    S.bnd_nbmask[p] = 0u;
     if (type == kInlet) {
         const int a = S.in_axis;
         const int coord = a == 0 ? x : a == 1 ? y : z;
@@ -243,8 +161,7 @@ __global__ void setup_mask(const SetupParams S)
             const double dy = a == 1 ? 0.0 : py - S.in_center[1];
             const double dz = a == 2 ? 0.0 : pz - S.in_center[2];
             const double prof = 1.0 - (dx * dx + dy * dy + dz * dz) / (S.in_radius * S.in_radius);
-            S.bnd_prof[p - S.n_bulk] = (float)(2.0 * (prof > 0.0 ? prof : 0.0));
-            S.bnd_nbmask[p - S.n_bulk] = 0u;
+            S.bnd_prof[p] = (float)(2.0 * (prof > 0.0 ? prof : 0.0));
         }
     } else if (type == kOutlet) {
         const int a = S.out_axis;
@@ -261,52 +178,21 @@ __global__ void setup_mask(const SetupParams S)
             if (ok) {
                 const long long nb = bx + (long long)S.nx * (by + (long long)S.ny * bz);
                 ok = S.flags[nb] == 1 && S.phi[nb] == 1.0f;
-                if (ok) S.bnd_nbmask[p - S.n_bulk] = link_mask<Q>(S, bx, by, bz, kBulk);
+                if (ok) S.bnd_nbmask[p] = link_mask<Q>(S, bx, by, bz, kBulk);
             }
-            S.bnd_prof[p - S.n_bulk] = 0.0f;
         }
         if (!ok) err |= kErrOutlet;
     }
     if (err) {
-        // keep the first offending cell for the error message: err[1] = 1 + list
-        // position, err[2] = packed coordinates, err[3] = porosity bits,
-        // err[4] = inlet reason bits
+        // keep the first offending cell for the error message: err[1] = 1 + slot,
+        // err[2] = packed coordinates x | y << 10 | z << 20, err[3] = porosity
+        // bits, err[4] = inlet reason bits
         if (atomicCAS(S.err + 1, 0u, (uint32_t)p + 1u) == 0u) {
-            S.err[2] = pc;
+            S.err[2] = (uint32_t)x | ((uint32_t)y << 10) | ((uint32_t)z << 20);
             S.err[3] = __float_as_uint(phi);
             S.err[4] = err >> 8;
         }
         atomicOr(S.err, err & 0xffu);
-    }
-}
-
-
-// Rest state: all deviations zero (f_i = w_i phi, rho = 1, u = 0) and the
-// relaxation rate of mu0 at rho = 1.
-template <class T>
-__global__ void init_state(const uint32_t* __restrict__ cells, int n_cells, int nx, int ny, long long N, int Q,
-                           T* __restrict__ f, float* __restrict__ omega, float omega0)
-{
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_cells) return;
-    const long long idx = cells[p] & ~kGhostFlag;
-    for (int i = 0; i < Q; ++i) f[(long long)i * N + idx] = T(0.0f);
-    omega[p] = omega0;
-}
-
-// Checkpoints in list order: state[i][p] = f[i][idx(p)] (raw storage type).
-template <class T>
-__global__ void pack_state(const uint32_t* __restrict__ cells, int n_cells, int nx, int ny, long long N, int Q,
-                           const T* __restrict__ f, T* __restrict__ state, int unpack, T* __restrict__ fout,
-                           const T* __restrict__ state_in)
-{
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_cells) return;
-    const long long idx = cells[p] & ~kGhostFlag;
-    if (unpack) {
-        for (int i = 0; i < Q; ++i) fout[(long long)i * N + idx] = state_in[(long long)i * n_cells + p];
-    } else {
-        for (int i = 0; i < Q; ++i) state[(long long)i * n_cells + p] = f[(long long)i * N + idx];
     }
 }
 
@@ -354,40 +240,56 @@ __global__ void fill_f32(float* p, long long n, float v)
     if (i < n) p[i] = v;
 }
 
-// Number of listed non-ghost cells whose region byte is set.
-__global__ void region_count(const uint32_t* cells, int n_cells, const uint8_t* region, unsigned long long* out)
+// Number of non-ghost slots whose region byte (dense) is set.
+__global__ void region_count(const uint32_t* __restrict__ rows, const int* __restrict__ rowbase,
+                             const uint32_t* __restrict__ mask, int n_store, int nx, const uint8_t* __restrict__ region,
+                             unsigned long long* out)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     int hit = 0;
-    if (p < n_cells) {
-        const uint32_t e = cells[p];
-        hit = !(e & kGhostFlag) && region[e] ? 1 : 0;
+    if (p < n_store && !(mask[p] & kGhostBit)) {
+        const uint32_t r = rows[p];
+        hit = region[(long long)(p - rowbase[r]) + (long long)nx * r] ? 1 : 0;
     }
     const unsigned int warp_hits = __popc(__ballot_sync(0xffffffffu, hit));
     if ((threadIdx.x & 31) == 0 && warp_hits) atomicAdd(out, (unsigned long long)warp_hits);
 }
 
-// Host launchers (kernel templates cannot be launched across translation units).
-cudaError_t launch_fill_f32(float* p, long long n, float v, cudaStream_t s)
+// dst[dense index of p] = src[p] for every non-ghost slot p.
+__global__ void scatter_f64(const uint32_t* __restrict__ rows, const int* __restrict__ rowbase,
+                            const uint32_t* __restrict__ mask, int n_store, int nx, const double* __restrict__ src,
+                            double* __restrict__ dst)
 {
-    if (n == 0) return cudaSuccess;
-    fill_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, v);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_store || (mask[p] & kGhostBit)) return;
+    const uint32_t r = rows[p];
+    dst[(long long)(p - rowbase[r]) + (long long)nx * r] = src[p];
+}
+
+// Host launchers (kernel templates cannot be launched across translation units).
+cudaError_t launch_setup_rows(const uint8_t* flags, int nx, int nrows, int* xmin, int* ext, uint32_t* err,
+                              cudaStream_t s)
+{
+    if (nrows == 0) return cudaSuccess;
+    const int per_block = kSetupThreads / 32;
+    setup_rows<<<(nrows + per_block - 1) / per_block, kSetupThreads, 0, s>>>(flags, nx, nrows, xmin, ext, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_region_count(const uint32_t* cells, int n_cells, const uint8_t* region, unsigned long long* out,
-                                cudaStream_t s)
+cudaError_t launch_setup_slots(const float* phi, int nx, int nrows, const int* rowbase, const int* xmin,
+                               const int* ext, uint32_t* rows, float* phi_s, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess || n_cells == 0) return e;
-    region_count<<<(n_cells + 255) / 256, 256, 0, s>>>(cells, n_cells, region, out);
+    if (nrows == 0) return cudaSuccess;
+    const int per_block = kSetupThreads / 32;
+    setup_slots<<<(nrows + per_block - 1) / per_block, kSetupThreads, 0, s>>>(phi, nx, nrows, rowbase, xmin, ext,
+                                                                              rows, phi_s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_setup_mask(int q, const SetupParams& S, cudaStream_t s)
 {
-    if (S.n_cells == 0) return cudaSuccess;
-    const int g = (S.n_cells + 255) / 256;
+    if (S.n_store == 0) return cudaSuccess;
+    const int g = (S.n_store + 255) / 256;
     if (q == 19)
         setup_mask<19><<<g, 256, 0, s>>>(S);
     else
@@ -395,53 +297,27 @@ cudaError_t launch_setup_mask(int q, const SetupParams& S, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_state(int storage, const uint32_t* cells, int n_cells, int nx, int ny, long long N, int Q,
-                              void* f, float* omega, float omega0, cudaStream_t s)
+cudaError_t launch_fill_f32(float* p, long long n, float v, cudaStream_t s)
 {
-    if (n_cells == 0) return cudaSuccess;
-    const int g = (n_cells + 255) / 256;
-    if (storage == 0)
-        init_state<float><<<g, 256, 0, s>>>(cells, n_cells, nx, ny, N, Q, static_cast<float*>(f), omega, omega0);
-    else if (storage == 1)
-        init_state<__half><<<g, 256, 0, s>>>(cells, n_cells, nx, ny, N, Q, static_cast<__half*>(f), omega, omega0);
-    else
-        init_state<__nv_bfloat16><<<g, 256, 0, s>>>(cells, n_cells, nx, ny, N, Q, static_cast<__nv_bfloat16*>(f),
-                                                     omega, omega0);
+    if (n == 0) return cudaSuccess;
+    fill_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, v);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_state(int storage, const uint32_t* cells, int n_cells, int nx, int ny, long long N, int Q,
-                              void* f, void* state, int unpack, cudaStream_t s)
+cudaError_t launch_region_count(const uint32_t* rows, const int* rowbase, const uint32_t* mask, int n_store, int nx,
+                                const uint8_t* region, unsigned long long* out, cudaStream_t s)
 {
-    if (n_cells == 0) return cudaSuccess;
-    const int g = (n_cells + 255) / 256;
-    if (storage == 0)
-        pack_state<float><<<g, 256, 0, s>>>(cells, n_cells, nx, ny, N, Q, static_cast<const float*>(f),
-                                             static_cast<float*>(state), unpack, static_cast<float*>(f),
-                                             static_cast<const float*>(state));
-    else if (storage == 1)
-        pack_state<__half><<<g, 256, 0, s>>>(cells, n_cells, nx, ny, N, Q, static_cast<const __half*>(f),
-                                              static_cast<__half*>(state), unpack, static_cast<__half*>(f),
-                                              static_cast<const __half*>(state));
-    else
-        pack_state<__nv_bfloat16><<<g, 256, 0, s>>>(cells, n_cells, nx, ny, N, Q,
-                                                     static_cast<const __nv_bfloat16*>(f),
-                                                     static_cast<__nv_bfloat16*>(state), unpack,
-                                                     static_cast<__nv_bfloat16*>(f),
-                                                     static_cast<const __nv_bfloat16*>(state));
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n_store == 0) return e;
+    region_count<<<(n_store + 255) / 256, 256, 0, s>>>(rows, rowbase, mask, n_store, nx, region, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_setup_cells(const uint8_t* flags, long long N, const CellGrid& G, uint32_t* counts,
-                               uint32_t* offsets, uint32_t* totals, cudaStream_t s, int phase, uint32_t* cells)
+cudaError_t launch_scatter_f64(const uint32_t* rows, const int* rowbase, const uint32_t* mask, int n_store, int nx,
+                               const double* src, double* dst, cudaStream_t s)
 {
-    const int nblk = (int)((N + kSetupChunk - 1) / kSetupChunk);
-    if (phase == 0) {
-        setup_count<<<nblk, kSetupThreads, 0, s>>>(flags, N, G, nblk, counts);
-        setup_scan<<<1, 1024, 0, s>>>(counts, nblk, offsets, totals);
-    } else {
-        setup_emit<<<nblk, kSetupThreads, 0, s>>>(flags, N, G, nblk, offsets, cells);
-    }
+    if (n_store == 0) return cudaSuccess;
+    scatter_f64<<<(n_store + 255) / 256, 256, 0, s>>>(rows, rowbase, mask, n_store, nx, src, dst);
     return cudaGetLastError();
 }
 

@@ -41,15 +41,31 @@ def test_workspace_size_host_logic():
 
     flags = np.ascontiguousarray(pipe_problem().flags)
     n_list = lbm.lbm_list_length(g, flags.ctypes.data)
-    assert 39424 < n_list < 32 * 32 * 64  # fluid cells plus ghost entries
+    assert n_list == 39424  # a circular cross-section: every row span is all fluid
     tight = lbm.lbm_workspace_size(g, n_list)
-    assert full > tight > 2 * 19 * 32 * 32 * 64 * 4
+    assert full > tight > 2 * 19 * n_list * 4
     g16 = lbm.make_grid((32, 32, 64), 19, "f16dev", (0, 0, 1))
     assert lbm.lbm_workspace_size(g16, 39424) < tight
     bad = lbm.make_grid((32, 32, 64), 20, "f32", (0, 0, 1))
     assert lbm.lbm_workspace_size(bad, 10) == 0
     huge = lbm.make_grid((2048, 2, 2), 19, "f32", (0, 0, 0))
     assert lbm.lbm_workspace_size(huge, 10) == 0
+
+
+def test_list_length_counts_row_spans():
+    """Spans run from the first to the last non-solid cell of each x-row; solid
+    cells inside a span count, rows without fluid do not."""
+    from paper_2402_10809_gb300 import lbm
+    import numpy as np
+
+    flags = np.zeros((3, 4, 10), np.uint8)
+    flags[0, 1, 2:5] = 1          # span 3
+    flags[1, 2, [1, 7]] = 1       # span 7 (five solid cells inside)
+    flags[2, 3, 9] = 3            # span 1
+    g = lbm.make_grid((10, 4, 3), 19, "f32", (0, 0, 0))
+    assert lbm.lbm_list_length(g, flags.ctypes.data) == 11
+    flags[2, 0, 0] = 7            # not a valid flag: not counted
+    assert lbm.lbm_list_length(g, flags.ctypes.data) == 11
 
 
 def test_init_rejects_bad_arguments_before_any_device_work():
