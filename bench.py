@@ -268,7 +268,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{name} D3Q27 {st0}-stored, {L} time steps per step, "
-                               f"{nf} fluid cells, Carreau-Yasuda, porous sac, pulsatile inlet",
+                               f"{nf} fluid cells, Carreau-Yasuda (lambda {prob.rheology['lam'] * 1e3:g} ms), "
+                               f"porous sac, pulsatile inlet",
                    "box": [n] * 3, "fluid_cells": nf, "time_steps_per_step": L,
                    "q": WORKLOAD["q"], "storage": st0, "parallelism": f"replicas{ws}",
                    "l2": f"{bpu * nf / 1e6:.0f} MB touched per time step and a 256 MB L2 flush "

@@ -91,7 +91,7 @@ def test_reference_gradient_matches_finite_differences():
     T = 16
     J, grad = TorchLBM(prob).gradient(prob.phi, T, prob.region)
     J0 = Oracle(prob).run_objective(T, prob.region)
-    assert abs(J - J0) < 1e-13 * abs(J0)
+    assert abs(J - J0) < 1e-12 * abs(J0)  # FP64 rounding of two summation orders (1.3e-13 seen)
     rng = np.random.default_rng(1)
     cand = np.argwhere((prob.region > 0) & (prob.flags > 0) & (prob.phi < 0.99) & (prob.phi > 0.61))
     scale = np.abs(grad).max()
