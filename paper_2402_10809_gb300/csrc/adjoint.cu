@@ -34,7 +34,11 @@ cudaError_t LBM_LAUNCHER(int what, const AdjParams& A, cudaStream_t s)
     if (what == 0) {
         const int grid = total_blocks(A.F);
         if (grid == 0) return cudaSuccess;
-        adjoint_kernel<LBM_Q, LBM_T><<<grid, kBlock, 0, s>>>(A);
+        constexpr size_t smem = adjoint_smem_bytes<LBM_Q>();
+        static const cudaError_t attr = cudaFuncSetAttribute(adjoint_kernel<LBM_Q, LBM_T>,
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (attr != cudaSuccess) return attr;
+        adjoint_kernel<LBM_Q, LBM_T><<<grid, kBlock, smem, s>>>(A);
     } else {
         if (A.n_out == 0) return cudaSuccess;
         adjoint_outlet_fixup<LBM_Q><<<(A.n_out + 127) / 128, 128, 0, s>>>(A);

@@ -289,9 +289,13 @@ __device__ __forceinline__ void outlet_adjoint(const AdjParams& A, const Coords&
 // forward quantities from S(t-1), omega(t-1), form the adjoints of the pulled
 // populations and write them to lambda(t-1) at the source slots; add the
 // cell's dJ/dphi terms; write mu(t-1).  jv accumulates the objective term.
+// park / lampark / dpark: this thread's columns of three Q x kBlock shared
+// arrays (pulled populations, lambda(t) at the cell's slots, rho(t-1) - 1 at
+// its pull sources), all filled by asynchronous copies issued at the start so
+// that their latencies overlap.
 template <int Q, class T, bool fast>
 __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t mask, volatile float* park,
-                                             double& jv)
+                                             volatile float* lampark, volatile float* dpark, double& jv)
 {
     using L = Lattice<Q>;
     const Params& P = A.F;
@@ -305,19 +309,42 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     uint32_t row = 0;
     {
         float g[Q];
+        constexpr bool f32 = sizeof(T) == 4;
+        if (!A.first) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) cp_async4(lampark + i * kBlock, A.lam_in + (size_t)i * n + p);
+        }
         if (fast) {
             row = P.rows[p];
             rb = row_bases(P, row);
             x = p - rb.b[4];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const uint32_t o = ((mask >> i) & 1u) ? (uint32_t)opp(i) * n + (uint32_t)p
-                                                      : (uint32_t)i * n + lean_slot(rb, x, -L::cx(i), -L::cy(i), -L::cz(i));
-                g[i] = Store<T>::ld(fs + o);
+                const bool bb = ((mask >> i) & 1u) != 0u;
+                const uint32_t src = lean_slot(rb, x, -L::cx(i), -L::cy(i), -L::cz(i));
+                const uint32_t o = bb ? (uint32_t)opp(i) * n + (uint32_t)p : (uint32_t)i * n + src;
+                if (f32)
+                    cp_async4(park + i * kBlock, reinterpret_cast<const float*>(fs) + o);
+                else
+                    g[i] = Store<T>::ld(fs + o);
+                if (!A.last && !bb && i != 0) cp_async4(dpark + i * kBlock, A.drho_prev + src);
+            }
+            cp_async_wait_all();
+            if (f32) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) g[i] = park[i * kBlock];
             }
         } else {
             cg = coords_of(P, p);
+            if (!A.last) {
+#pragma unroll
+                for (int i = 1; i < Q; ++i)
+                    if (!((mask >> i) & 1u))
+                        cp_async4(dpark + i * kBlock,
+                                  A.drho_prev + shifted(P, cg, -L::cx(i), -L::cy(i), -L::cz(i)));
+            }
             pull_general<Q, T>(P, fs, cg, mask, g);
+            cp_async_wait_all();
             type = (mask >> kTypeShift) & 3u;
             if (type == kInlet) {
                 zou_he<Q>(P, P.bnd_prof[p], g);
@@ -369,13 +396,12 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     MacroBar b{};
     float omb = 0.0f, phib = 0.0f;
     if (!A.first) {
-        const float* __restrict__ la = A.lam_in + p;
         float h[Q];
         float Ag = 0.0f, Wd = 0.0f, Aphi = 0.0f;
         const bool porous = (mask & kPorousBit) != 0u;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float a = __ldcs(la + (size_t)i * n);
+            const float a = lampark[i * kBlock];
             Ag = fmaf(a, park[i * kBlock], Ag);
             park[i * kBlock] = a;
             h[i] = L::w(i) * a;
@@ -516,12 +542,10 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
             if (fast) {
                 const uint32_t src = lean_slot(rb, x, -L::cx(i), -L::cy(i), -L::cz(i));
                 lo[bb ? (uint32_t)opp(i) * n + (uint32_t)p : (uint32_t)i * n + src] = v;
-                if (!bb && i != 0) gat = fmaf(L::w(i) * __ldg(A.drho_prev + src), v, gat);
+                if (!bb && i != 0) gat = fmaf(L::w(i) * dpark[i * kBlock], v, gat);
             } else {
                 lo[pull_offset<Q>(P, cg, mask, i)] = v;
-                if (!bb && i != 0)
-                    gat = fmaf(L::w(i) * __ldg(A.drho_prev + shifted(P, cg, -L::cx(i), -L::cy(i), -L::cz(i))), v,
-                               gat);
+                if (!bb && i != 0) gat = fmaf(L::w(i) * dpark[i * kBlock], v, gat);
             }
         }
         gacc += (double)gat;
@@ -532,9 +556,16 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
 
 template <int Q, class T>
 __device__ __noinline__ void adjoint_general(const AdjParams& A, int p, uint32_t mask, volatile float* park,
-                                             double& jv)
+                                             volatile float* lampark, volatile float* dpark, double& jv)
 {
-    adjoint_cell<Q, T, false>(A, p, mask, park, jv);
+    adjoint_cell<Q, T, false>(A, p, mask, park, lampark, dpark, jv);
+}
+
+// Dynamic shared memory of adjoint_kernel: three Q x kBlock float arrays.
+template <int Q>
+constexpr size_t adjoint_smem_bytes()
+{
+    return (size_t)3 * Q * kBlock * sizeof(float);
 }
 
 template <int Q, class T>
@@ -542,21 +573,24 @@ __global__ void __launch_bounds__(kBlock, 2) adjoint_kernel(const AdjParams A)
 {
     const Params& P = A.F;
     const int nbg = general_blocks(P);
-    __shared__ float sg[Q * kBlock];
-    volatile float* park = sg + threadIdx.x;
+    extern __shared__ float adj_smem[];
+    volatile float* park = adj_smem + threadIdx.x;
+    volatile float* lampark = park + Q * kBlock;
+    volatile float* dpark = park + 2 * Q * kBlock;
     double jv = 0.0;
     if ((int)blockIdx.x < nbg) {
         const int k = (int)blockIdx.x * P.gen_block + (int)threadIdx.x;
         if ((int)threadIdx.x < P.gen_block && k < P.n_general) {
             const int p = (int)P.general[k];
-            adjoint_general<Q, T>(A, p, P.mask[p], park, jv);
+            adjoint_general<Q, T>(A, p, P.mask[p], park, lampark, dpark, jv);
         }
     } else {
         const int p = ((int)blockIdx.x - nbg) * kBlock + (int)threadIdx.x;
         if (p < P.n_store) {
             const uint32_t mask = P.mask[p];
             // ghost slots hold no state; general cells belong to the general blocks
-            if (!(mask & (kGhostBit | kGeneralBits)) && !P.wide) adjoint_cell<Q, T, true>(A, p, mask, park, jv);
+            if (!(mask & (kGhostBit | kGeneralBits)) && !P.wide)
+                adjoint_cell<Q, T, true>(A, p, mask, park, lampark, dpark, jv);
         }
     }
     if (A.objective) {

@@ -129,6 +129,19 @@ struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
 };
 
+// 4-byte global -> shared copy that stays in flight without occupying a
+// register (LDGSTS, sm_80 and later); cp_async_wait_all commits the thread's
+// copies and waits for them.
+__device__ __forceinline__ void cp_async4(volatile float* dst, const float* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared((const void*)dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // c . v for a lattice vector c with components in {-1, 0, 1}: only the needed
 // additions and sign flips (after unrolling every branch is decided at compile
 // time; IEEE arithmetic would not let the compiler drop 0 * v or v + 0).
