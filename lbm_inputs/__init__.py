@@ -23,8 +23,10 @@ from .configs import (  # noqa: F401
     Problem,
     pipe_problem,
     aneurysm_problem,
+    coil_problem,
     channel_problem,
     periodic_box_problem,
     BASELINE_CY,
+    ANEURYSM_LAMBDA,
     PAPER_TABLE1,
 )
