@@ -300,6 +300,10 @@ def run_ours(args):
 
 
 ADJOINT = dict(name="aneurysm128", n=128, q=27, T=500, K=50, seed=0)
+# Algorithmic bytes of one reverse fluid-cell update (D3Q27, FP32): pull of
+# S(t-1), lambda(t) read, lambda(t-1) write (3 x 108), omega 4, mu read + write
+# 8, phi 4, mask 4, rho - 1 gather 4, dJ/dphi read-modify-write 16.
+ADJOINT_BYTES_PER_UPDATE = 364
 
 
 def adjoint_cost(torch, lbm, args):
@@ -349,6 +353,14 @@ def adjoint_cost(torch, lbm, args):
         t_adj, J = timed(run, 3)
         res[name] = {"K": k, "seconds": t_adj, "cost_vs_forward": t_adj / t_fwd, "J": J,
                      "workspace_gb": nbytes / 1e9}
+        if k >= T:
+            # no replay: the reverse sweep is the adjoint time minus the T forward steps
+            t_rev = (t_adj - t_fwd) / (T + 1)
+            peak, _ = load_peaks()
+            bytes_rev = ADJOINT_BYTES_PER_UPDATE * prob.n_fluid
+            res[name].update({"reverse_step_us": 1e6 * t_rev, "reverse_vs_forward_step": t_rev / (t_fwd / T),
+                              "reverse_bytes_per_update": ADJOINT_BYTES_PER_UPDATE,
+                              "reverse_roofline_frac": bytes_rev / t_rev / 1e9 / peak})
         del ws
     sim.close()
     return res
