@@ -28,7 +28,7 @@
 
 namespace lbm {
 
-// what = 0: reverse time step; what = 1: outlet fix-up.
+// what = 0: reverse time step; 1: outlet fix-up; 2: outlet ordinals (once per call).
 cudaError_t LBM_LAUNCHER(int what, const AdjParams& A, cudaStream_t s)
 {
     if (what == 0) {
@@ -39,9 +39,12 @@ cudaError_t LBM_LAUNCHER(int what, const AdjParams& A, cudaStream_t s)
                                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (attr != cudaSuccess) return attr;
         adjoint_kernel<LBM_Q, LBM_T><<<grid, kBlock, smem, s>>>(A);
-    } else {
+    } else if (what == 1) {
         if (A.n_out == 0) return cudaSuccess;
         adjoint_outlet_fixup<LBM_Q><<<(A.n_out + 127) / 128, 128, 0, s>>>(A);
+    } else {
+        if (A.n_out == 0) return cudaSuccess;
+        adjoint_outlet_ordinals<LBM_Q><<<(A.n_out + 127) / 128, 128, 0, s>>>(A);
     }
     return cudaGetLastError();
 }

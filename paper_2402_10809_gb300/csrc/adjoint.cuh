@@ -43,21 +43,19 @@ struct AdjParams {
     int objective;          // t >= 1: the kinetic-energy term of time t belongs to J
     int last;               // t = 0: S(-1) and omega(-1) are constants
     const uint32_t* out_slots;  // [n_out] slots of the outlet cells, ascending
+    uint32_t* out_ord;          // [n_store] ordinal of each outlet slot in out_slots (others unused)
     int n_out;
     float* bnd_delta;       // [Q][n_out]: outlet contributions to the neighbour's slots
     double* bnd_dphi;       // [n_out]: outlet contribution to the neighbour's porosity
-    double* jpart;          // [blocks]: per-block sums of the objective (accumulated over launches)
+    double* jpart;          // [blocks][kBlock / 32]: per-warp sums of the objective (accumulated over launches)
 };
 
-// Ordinal of outlet slot p in the ascending outlet list.
-__device__ __forceinline__ int outlet_ordinal(const AdjParams& A, int p)
+// out_ord[out_slots[q]] = q, once per adjoint call.
+template <int Q>
+__global__ void adjoint_outlet_ordinals(const AdjParams A)
 {
-    int lo = 0, hi = A.n_out - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((int)A.out_slots[mid] < p) lo = mid + 1; else hi = mid;
-    }
-    return lo;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < A.n_out) A.out_ord[A.out_slots[q]] = (uint32_t)q;
 }
 
 // ------------------------------------------------------------------ pieces
@@ -229,7 +227,7 @@ __device__ __forceinline__ void outlet_adjoint(const AdjParams& A, const Coords&
     const int ax = P.out_axis;
     const int sgn = P.out_side == 1 ? -1 : 1;
     const uint32_t nbmask = P.bnd_nbmask[p];
-    const int q = outlet_ordinal(A, p);
+    const int q = (int)A.out_ord[p];
     const Coords nc = make_coords(P, c.x + (ax == 0 ? sgn : 0), c.y + (ax == 1 ? sgn : 0), c.z + (ax == 2 ? sgn : 0));
     const float phin = __ldg(P.phi + nc.slot);
     const T* f = static_cast<const T*>(P.fsrc);
@@ -292,7 +290,8 @@ __device__ __forceinline__ void outlet_adjoint(const AdjParams& A, const Coords&
 // park / lampark / dpark: this thread's columns of three Q x kBlock shared
 // arrays (pulled populations, lambda(t) at the cell's slots, rho(t-1) - 1 at
 // its pull sources), all filled by asynchronous copies issued at the start so
-// that their latencies overlap.
+// that their latencies overlap; the per-cell scalars are loaded before any
+// wait for the same reason.
 template <int Q, class T, bool fast>
 __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t mask, volatile float* park,
                                              volatile float* lampark, volatile float* dpark, double& jv)
@@ -300,6 +299,10 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     using L = Lattice<Q>;
     const Params& P = A.F;
     const float phi = __ldg(P.phi + p);
+    const float om_prev = P.omega[p];
+    const float bmu = A.first ? 0.0f : A.mu[p];
+    const double gphi0 = A.gphi[p];
+    const bool porous = (mask & kPorousBit) != 0u;
     const T* __restrict__ fs = static_cast<const T*>(P.fsrc);
     const uint32_t n = (uint32_t)P.n_store;
     int type = kBulk;
@@ -330,10 +333,6 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
                 if (!A.last && !bb && i != 0) cp_async4(dpark + i * kBlock, A.drho_prev + src);
             }
             cp_async_wait_all();
-            if (f32) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) g[i] = park[i * kBlock];
-            }
         } else {
             cg = coords_of(P, p);
             if (!A.last) {
@@ -343,6 +342,7 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
                         cp_async4(dpark + i * kBlock,
                                   A.drho_prev + shifted(P, cg, -L::cx(i), -L::cy(i), -L::cz(i)));
             }
+
             pull_general<Q, T>(P, fs, cg, mask, g);
             cp_async_wait_all();
             type = (mask >> kTypeShift) & 3u;
@@ -352,8 +352,10 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
                 outlet<Q, T>(P, cg, phi, P.bnd_nbmask[p], g);
             }
         }
+        if (!(fast && f32)) {  // the FP32 lean pull already sits in park
 #pragma unroll
-        for (int i = 0; i < Q; ++i) park[i * kBlock] = g[i];
+            for (int i = 0; i < Q; ++i) park[i * kBlock] = g[i];
+        }
     }
     // ---- forward recompute (as in cell_impl)
     float smx, smy, smz;
@@ -377,7 +379,6 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
         pyz = fmaf(M.uy, fmaf(-M.sigma, M.uz, 0.5f * M.Fz), fmaf(0.5f * M.Fy, M.uz, m.syz));
     }
     const float pn = sqrtf(fmaf(pxx, pxx, fmaf(pyy, pyy, fmaf(pzz, pzz, 2.0f * fmaf(pxy, pxy, fmaf(pxz, pxz, pyz * pyz))))));
-    const float om_prev = P.omega[p];
     const float irho = __fdividef(1.0f, M.rho);
     const float gdot = 3.0f * om_prev * pn * irho;
     // Carreau-Yasuda viscosity and rate with the pieces of their derivatives
@@ -398,29 +399,23 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     if (!A.first) {
         float h[Q];
         float Ag = 0.0f, Wd = 0.0f, Aphi = 0.0f;
-        const bool porous = (mask & kPorousBit) != 0u;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const float a = lampark[i * kBlock];
             Ag = fmaf(a, park[i * kBlock], Ag);
-            park[i * kBlock] = a;
             h[i] = L::w(i) * a;
             // the link term exists where y + c_i (i != 0) is a fluid cell that
             // pulls from y (mask bit of the opposite direction clear)
             if (i != 0 && !((mask >> opp(i)) & 1u)) {
                 Wd += h[i];
                 if (porous) {
-                    uint32_t ni;
-                    if (fast)
-                        ni = lean_slot(rb, x, L::cx(i), L::cy(i), L::cz(i));
-                    else
-                        ni = (uint32_t)shifted(P, cg, L::cx(i), L::cy(i), L::cz(i));
+                    const uint32_t ni = fast ? lean_slot(rb, x, L::cx(i), L::cy(i), L::cz(i))
+                                             : (uint32_t)shifted(P, cg, L::cx(i), L::cy(i), L::cz(i));
                     Aphi = fmaf(h[i], __ldg(P.phi + ni) - phi, Aphi);
                 }
             }
         }
         const Moments<Q> am = moments<Q>(h);  // A0, A1, A2 = sums of w a, w a c, w a c c
-        const float bmu = A.mu[p];
         const float A0 = am.sd;
         const float uu = fmaf(M.ux, M.ux, fmaf(M.uy, M.uy, M.uz * M.uz));
         const float uF = fmaf(M.ux, M.Fx, fmaf(M.uy, M.Fy, M.uz * M.Fz));
@@ -454,9 +449,6 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
         b.Fy = h2 * Buy;
         b.Fz = h2 * Buz;
         phib = -M.drho * Wd;
-    } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) park[i * kBlock] = 0.0f;
     }
     // omega = 2 rho / (6 mu + rho)
     b.rho = omb * 12.0f * mu * iE * iE;
@@ -504,12 +496,11 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     const float sdb = macro_adjoint(P, phi, smx, smy, smz, M, b, mbx, mby, mbz, phib);
 
     // ---- adjoints of the populations after the boundary condition:
-    // gbar_i = (1 - omega) a_i + sdbar + mbar.c_i + c_i^T Pibar c_i
+    // gbar_i = (1 - omega) a_i + sdbar + mbar.c_i + c_i^T Pibar c_i (a = 0 at t = T)
     const float omo = 1.0f - om;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    auto gbar = [&](int i) {
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        float v = fmaf(omo, park[i * kBlock], sdb);
+        float v = A.first ? sdb : fmaf(omo, lampark[i * kBlock], sdb);
         if (cx) v += cx > 0 ? mbx : -mbx;
         if (cy) v += cy > 0 ? mby : -mby;
         if (cz) v += cz > 0 ? mbz : -mbz;
@@ -519,39 +510,49 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
         if (cx && cy) v += cx * cy > 0 ? 2.0f * bxy : -2.0f * bxy;
         if (cx && cz) v += cx * cz > 0 ? 2.0f * bxz : -2.0f * bxz;
         if (cy && cz) v += cy * cz > 0 ? 2.0f * byz : -2.0f * byz;
-        park[i * kBlock] = v;
-    }
-    if (!fast) {
+        return v;
+    };
+    double gacc = (double)phib;
+    float gat = 0.0f;
+    if (fast) {
+        // ---- transpose of the pull, written as each gbar_i is formed: lambda(t-1)
+        // at the source slots, plus the porosity-link gather
+        // w_i (rho(t-1, y - c_i) - 1) lambda(t-1)[y - c_i, i]
+        if (!A.last) {
+            float* __restrict__ lo = A.lam_out;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float v = gbar(i);
+                const bool bb = ((mask >> i) & 1u) != 0u;
+                const uint32_t src = lean_slot(rb, x, -L::cx(i), -L::cy(i), -L::cz(i));
+                lo[bb ? (uint32_t)opp(i) * n + (uint32_t)p : (uint32_t)i * n + src] = v;
+                if (!bb && i != 0) gat = fmaf(L::w(i) * dpark[i * kBlock], v, gat);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) park[i * kBlock] = gbar(i);
         if (type == kInlet) {
             zou_he_adjoint<Q>(P, P.bnd_prof[p], park, phib);
         } else if (type == kOutlet) {
             outlet_adjoint<Q, T>(A, cg, phi, p, park, phib);
         }
-    }
-
-    // ---- transpose of the pull: lambda(t-1) at the source slots, plus the
-    // porosity-link gather w_i (rho(t-1, y - c_i) - 1) lambda(t-1)[y - c_i, i]
-    double gacc = (double)phib;
-    if (!A.last) {
-        float* __restrict__ lo = A.lam_out;
-        float gat = 0.0f;
+        gacc = (double)phib;
+        if (!A.last) {
+            float* __restrict__ lo = A.lam_out;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float v = park[i * kBlock];
-            const bool bb = ((mask >> i) & 1u) != 0u;
-            if (fast) {
-                const uint32_t src = lean_slot(rb, x, -L::cx(i), -L::cy(i), -L::cz(i));
-                lo[bb ? (uint32_t)opp(i) * n + (uint32_t)p : (uint32_t)i * n + src] = v;
-                if (!bb && i != 0) gat = fmaf(L::w(i) * dpark[i * kBlock], v, gat);
-            } else {
+            for (int i = 0; i < Q; ++i) {
+                const float v = park[i * kBlock];
                 lo[pull_offset<Q>(P, cg, mask, i)] = v;
-                if (!bb && i != 0) gat = fmaf(L::w(i) * dpark[i * kBlock], v, gat);
+                if (!((mask >> i) & 1u) && i != 0) gat = fmaf(L::w(i) * dpark[i * kBlock], v, gat);
             }
         }
+    }
+    if (!A.last) {
         gacc += (double)gat;
         A.mu[p] = mu_prev;
     }
-    A.gphi[p] += gacc;
+    A.gphi[p] = gphi0 + gacc;
 }
 
 template <int Q, class T>
@@ -594,17 +595,11 @@ __global__ void __launch_bounds__(kBlock, 2) adjoint_kernel(const AdjParams A)
         }
     }
     if (A.objective) {
-        // block sum of the objective terms, added to this block's running partial
-        __shared__ double red[kBlock / 32];
+        // warp sum of the objective terms, added to this warp's running partial
+        // (one writer per slot: deterministic, no block barrier)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) jv += __shfl_xor_sync(0xffffffffu, jv, off);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = jv;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int w = 0; w < kBlock / 32; ++w) s += red[w];
-            A.jpart[blockIdx.x] += s;
-        }
+        if ((threadIdx.x & 31) == 0) A.jpart[(size_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5)] += jv;
     }
 }
 

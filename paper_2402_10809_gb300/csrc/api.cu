@@ -640,7 +640,7 @@ struct AdjLayout {
     int nseg = 0, Kh = 0;  // segments; history slots H[1..Kh]
     size_t sbytes = 0, wbytes = 0, lbytes = 0;
     size_t ck = 0, hist = 0, wck = 0, whist = 0, rck = 0, rhist = 0, lam[2] = {0, 0};
-    size_t mu = 0, gphi = 0, region = 0, jpart = 0, outs = 0, bdelta = 0, bdphi = 0, count = 0, end = 0;
+    size_t mu = 0, gphi = 0, region = 0, jpart = 0, outs = 0, ord = 0, bdelta = 0, bdphi = 0, count = 0, end = 0;
 };
 
 AdjLayout adj_layout(const lbm_ctx* c, int T, int K)
@@ -667,8 +667,9 @@ AdjLayout adj_layout(const lbm_ctx* c, int T, int K)
     A.mu = take(n * 4);
     A.gphi = take(n * 8);
     A.region = take(N);
-    A.jpart = take((size_t)(total_blocks(c->base) + 1) * 8);
+    A.jpart = take((size_t)(total_blocks(c->base) + 1) * (kBlock / 32) * 8);
     A.outs = take(no * 4);
+    A.ord = take(n * 4);
     A.bdelta = take(Q * no * 4);
     A.bdphi = take(no * 8);
     A.count = take(8);
@@ -740,7 +741,8 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, const uint8_
     LBM_CUDA(cudaMemsetAsync(grad, 0, N * 8, st), "clear gradient");
     LBM_CUDA(cudaMemsetAsync(gphi, 0, n * 8, st), "clear packed gradient");
     LBM_CUDA(cudaMemsetAsync(Cs(0), 0, AL.sbytes, st), "rest state");
-    LBM_CUDA(cudaMemsetAsync(jpart, 0, (size_t)(nblk + 1) * 8, st), "clear objective partials");
+    const size_t nparts = (size_t)nblk * (kBlock / 32);
+    LBM_CUDA(cudaMemsetAsync(jpart, 0, (nparts + 1) * 8, st), "clear objective partials");
     LBM_CUDA(launch_fill_f32(Wc(0), (long long)n, c->omega0, st), "initial omega");
 
     auto step = [&](long long t, const void* src, void* dst, float* om, float* drho) {
@@ -792,10 +794,12 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, const uint8_
     A.region = reg;
     A.kappa = (float)(1.0 / ((double)T * (double)cnt));
     A.out_slots = outs;
+    A.out_ord = reinterpret_cast<uint32_t*>(w + AL.ord);
     A.n_out = c->n_out;
     A.bnd_delta = reinterpret_cast<float*>(w + AL.bdelta);
     A.bnd_dphi = reinterpret_cast<double*>(w + AL.bdphi);
     A.jpart = jpart;
+    LBM_CUDA(launch_adj(c->grid, 2, A, st), "outlet ordinals");
     int li = 0;  // lam[li] holds lambda(t), lam[1 - li] receives lambda(t-1)
     for (int k = kl; k >= 0; --k) {
         const int s = k * K;
@@ -831,12 +835,12 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, const uint8_
         for (int t = e - 1; t >= s; --t) LBM_CUDA(reverse(t, 0), "adjoint reverse step");
     }
     LBM_CUDA(launch_scatter_f64(B.rows, B.rowbase, B.mask, c->n_store, c->grid.nx, gphi, grad, st), "gradient scatter");
-    std::vector<double> hp((size_t)nblk + 1, 0.0);
-    if (nblk > 0)
-        LBM_CUDA(cudaMemcpyAsync(hp.data(), jpart, (size_t)nblk * 8, cudaMemcpyDeviceToHost, st), "copy objective");
+    std::vector<double> hp(nparts + 1, 0.0);
+    if (nparts > 0)
+        LBM_CUDA(cudaMemcpyAsync(hp.data(), jpart, nparts * 8, cudaMemcpyDeviceToHost, st), "copy objective");
     LBM_CUDA(cudaStreamSynchronize(st), "adjoint sync");
     double sum = 0.0;
-    for (int b = 0; b < nblk; ++b) sum += hp[b];
+    for (size_t b = 0; b < nparts; ++b) sum += hp[b];
     *J = sum;
     return LBM_OK;
 }
