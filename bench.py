@@ -286,6 +286,8 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": args.steps * L,
     }
+    if rank == 0:
+        line["wall_shear"] = wall_shear_pass(torch, lbm, sim, prob, stream)
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = adjoint_cost(torch, lbm, args)
     if rank == 0 and not args.no_coil:
@@ -366,6 +368,32 @@ def adjoint_cost(torch, lbm, args):
         del ws
     sim.close()
     return res
+
+
+def wall_shear_pass(torch, lbm, sim, prob, stream):
+    """One pass of the voxel wall-shear-stress proxy (lbm_wall_shear, device
+    output) on the benchmark state: CUDA events around 5 passes, best taken.
+    Algorithmic bytes: the dense output (4 N, cleared and written), the slot
+    masks (4 n_store) and, per wall cell, its populations plus porosity, rate
+    and row id (Q s + 12)."""
+    out = torch.empty(prob.flags.shape, dtype=torch.float32, device="cuda")
+    lbm.lbm_wall_shear(sim.ctx, out.data_ptr(), 1)
+    best = 1e9
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lbm.lbm_wall_shear(sim.ctx, out.data_ptr(), 1)
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    n_wall = int((out > 0).sum().item())
+    n_store = lbm.lbm_list_length(sim.grid, np.ascontiguousarray(prob.flags).ctypes.data)
+    nbytes = 4 * prob.flags.size + 4 * n_store + n_wall * (prob.q * 4 + 12)
+    peak, _ = load_peaks()
+    return {"pass_us": 1e6 * best, "wall_cells": n_wall, "algorithmic_bytes": nbytes,
+            "roofline_frac": nbytes / best / 1e9 / peak, "unit": "lattice stress |tau|",
+            "max_wss": float(out.max().item())}
 
 
 def coil_study(torch, lbm, args):

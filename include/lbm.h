@@ -149,6 +149,18 @@ lbm_status lbm_moments(lbm_ctx* ctx, float* rho, float* u, float* shear_rate, fl
  * tells where it lives.  out is host memory; the call synchronises. */
 lbm_status lbm_diag(lbm_ctx* ctx, const uint8_t* region, int32_t region_on_device, double out[8]);
 
+/* Wall-shear-stress proxy of the current time t on the dense box (the
+ * quantity whose sac-wall average the paper reports beside the velocity,
+ * Sec. 4 results: tau = sigma n - (n . sigma n) n).  Voxel form: at a fluid
+ * cell with links to the wall (neighbours that are solid or outside the box),
+ * n is the normalised sum of w_i c_i over those links, sigma = -(1 - omega/2) Pi
+ * the viscous stress from the corrected second moment Pi of the shear rate,
+ * with omega the rate of the collision of time t.  wss [N] receives |tau| in
+ * lattice units (multiply by rho0 dx^2 / dt^2 for Pa); 0 on cells without wall
+ * links, on inlet / outlet cells and on solid cells.  dst_on_device: 1 device
+ * pointer (asynchronous), 0 host pointer (synchronises). */
+lbm_status lbm_wall_shear(lbm_ctx* ctx, float* wss, int32_t dst_on_device);
+
 /* lbm_diag without caller scratch (the paper has no counterpart; this is a
  * deployment convenience).  Same outputs as lbm_diag, computed by the same
  * kernels, but the per-block partial sums and the device-side result live in a

@@ -532,6 +532,63 @@ void oracle_moments(const oracle_ctx* o, double* rho, double* ux, double* uy, do
     }
 }
 
+/* Voxel wall-shear-stress proxy of the current time t (the paper evaluates
+ * tau = sigma n - (n . sigma n) n with the outer wall normal n on the wall
+ * surface, Sec. 4).  READING (voxel form): at a fluid cell with links to the
+ * wall (neighbours that are solid or outside the box, where the step bounces
+ * populations back), n = sum over those links of w_i c_i, normalised: the
+ * direction of the wall as seen from the cell; sigma = -(1 - omega(t)/2) Pi is
+ * the viscous stress recovered from the corrected second moment Pi of
+ * shear_rate, with omega(t) the rate of the collision of time t.  Output |tau|
+ * in lattice units on the dense box; 0 on cells without wall links, on
+ * inlet / outlet cells and on solid cells. */
+void oracle_wss(const oracle_ctx* o, double* wss)
+{
+    memset(wss, 0, o->n_box * sizeof(double));
+    int64_t nf = o->nf;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nf; ++k) {
+        int64_t idx = o->cell[k];
+        if (o->flags[idx] != O_FLUID) continue;
+        int x, y, z;
+        coords(o, idx, &x, &y, &z);
+        double nrm[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < o->q; ++i) {  /* the rest direction adds nothing */
+            int ax, sd;
+            int64_t d = neighbour(o, x, y, z, o->c[i], &ax, &sd);
+            if (d < 0 || o->flags[d] == O_SOLID)
+                for (int a = 0; a < 3; ++a) nrm[a] += o->w[i] * o->c[i][a];
+        }
+        double nn = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+        if (!(nn > 1e-12)) continue;
+        for (int a = 0; a < 3; ++a) nrm[a] /= nn;
+        double phi = o->phi[idx], r, u[3], F[3];
+        const double* f = o->f + k * o->q;
+        macroscopic(o, f, phi, &r, u, F);
+        double pi[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) pi[a][b] = 0.5 * (F[a] * u[b] + u[a] * F[b]);
+        for (int i = 0; i < o->q; ++i) {
+            double dv = f[i] - equilibrium(o, i, phi, r, u);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) pi[a][b] += dv * o->c[i][a] * o->c[i][b];
+        }
+        double gd = shear_rate(o, f, phi, r, u, F, o->omega[k]);
+        double om = omega_of(r, carreau_yasuda(o, gd));
+        double sn[3], nsn = 0.0, t2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            sn[a] = 0.0;
+            for (int b = 0; b < 3; ++b) sn[a] += -(1.0 - 0.5 * om) * pi[a][b] * nrm[b];
+            nsn += nrm[a] * sn[a];
+        }
+        for (int a = 0; a < 3; ++a) {
+            double ta = sn[a] - nsn * nrm[a];
+            t2 += ta * ta;
+        }
+        wss[idx] = sqrt(t2);
+    }
+}
+
 /* Diagnostics of the current time: out = {mass sum_x sum_i f_i, kinetic energy
  * sum rho |u|^2 / 2, sum of |u| over the region, region cell count, max |u|,
  * min omega(t), max omega(t), count of non-finite cells}.  region may be NULL

@@ -61,6 +61,8 @@ def lib():
             L.oracle_step.argtypes = [C.c_void_p, C.c_int64]
             L.oracle_moments.argtypes = [C.c_void_p, d, d, d, d, d, d]
             L.oracle_diag.argtypes = [C.c_void_p, P(C.c_uint8), d]
+            L.oracle_wss.restype = None
+            L.oracle_wss.argtypes = [C.c_void_p, C.c_void_p]
             L.oracle_run_objective.restype = C.c_double
             L.oracle_run_objective.argtypes = [C.c_void_p, C.c_int64, P(C.c_uint8)]
             L.oracle_nfluid.restype = C.c_int64
@@ -164,6 +166,12 @@ class Oracle:
         self.L.oracle_diag(self.h, reg.ctypes.data_as(C.POINTER(C.c_uint8)) if reg is not None else None,
                            _dptr(out))
         return out
+
+    def wall_shear(self):
+        """Voxel wall-shear-stress proxy |tau| of the current time (dense box)."""
+        out = np.zeros(int(np.prod(self.shape)))
+        self.L.oracle_wss(self.h, _dptr(out))
+        return out.reshape(self.shape)
 
     def run_objective(self, T, region):
         reg = np.ascontiguousarray(region, dtype=np.uint8)

@@ -23,6 +23,7 @@ cudaError_t launch_step_19_bf16(int, const Params&, cudaStream_t);
 cudaError_t launch_step_27_f32(int, const Params&, cudaStream_t);
 cudaError_t launch_step_27_f16(int, const Params&, cudaStream_t);
 cudaError_t launch_step_27_bf16(int, const Params&, cudaStream_t);
+cudaError_t launch_wall_shear(int q, int storage, const Params& P, float* out, int compact, cudaStream_t s);
 cudaError_t launch_adjoint_19_f32(int, const AdjParams&, cudaStream_t);
 cudaError_t launch_adjoint_19_f16(int, const AdjParams&, cudaStream_t);
 cudaError_t launch_adjoint_19_bf16(int, const AdjParams&, cudaStream_t);
@@ -543,6 +544,35 @@ extern "C" lbm_status lbm_diag(lbm_ctx* c, const uint8_t* region, int32_t region
         }
     }
     return run_diag(c, reg, out);
+}
+
+extern "C" lbm_status lbm_wall_shear(lbm_ctx* c, float* wss, int32_t dst_on_device)
+{
+    if (!c || !wss) return LBM_EINVAL;
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    Params P = c->base;
+    P.fsrc = c->f(c->cur);
+    P.fdst = nullptr;
+    P.t = c->t;
+    const size_t N = (size_t)c->N;
+    if (dst_on_device) {
+        LBM_CUDA(cudaMemsetAsync(wss, 0, N * 4, c->stream), "clear wall shear");
+        LBM_CUDA(launch_wall_shear(c->grid.q, c->grid.storage, P, wss, 0, c->stream), "wall shear kernel");
+        return LBM_OK;
+    }
+    const size_t n = (size_t)c->n_store;
+    float* st = c->at<float>(c->L.staging);
+    std::vector<float> h(n);
+    if (n > 0) {
+        LBM_CUDA(cudaMemsetAsync(st, 0, n * 4, c->stream), "clear wall shear");
+        LBM_CUDA(launch_wall_shear(c->grid.q, c->grid.storage, P, st, 1, c->stream), "wall shear kernel");
+        LBM_CUDA(cudaMemcpyAsync(h.data(), st, n * 4, cudaMemcpyDeviceToHost, c->stream), "wall shear copy");
+    }
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "wall shear sync");
+    std::memset(wss, 0, N * 4);
+    for (size_t p = 0; p < n; ++p)
+        if (c->host_idx[p] >= 0) wss[c->host_idx[p]] = h[p];
+    return LBM_OK;
 }
 
 extern "C" lbm_status lbm_set_check(lbm_ctx* c, int32_t check_every)

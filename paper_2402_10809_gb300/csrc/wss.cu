@@ -1,0 +1,84 @@
+// Voxel wall-shear-stress proxy of the current time (the quantity whose sac
+// average the paper reports beside the velocity, Sec. 4 results: the wall
+// shear stress tau = sigma n - (n . sigma n) n).
+//
+// Voxel form: at a bulk cell with links to the wall (directions whose
+// neighbour is solid or outside the box, the links the step bounces back),
+// n = sum over those links of w_i c_i, normalised (the direction of the wall
+// as seen from the cell); sigma = -(1 - omega(t)/2) Pi is the viscous stress
+// recovered from the corrected second moment Pi that also gives the shear rate
+// (Sec. 3), with omega(t) the rate of the collision of time t.  The output is
+// |tau| in lattice units; cells without wall links, inlet and outlet cells stay
+// at the caller's zero.  One thread per slot; only wall cells do any work, so
+// the pass uses the general-path addressing for all of them.
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace lbm {
+
+template <int Q, class T>
+__global__ void __launch_bounds__(kBlock) wall_shear_kernel(const Params P, float* __restrict__ out, int compact)
+{
+    using L = Lattice<Q>;
+    const int p = (int)blockIdx.x * kBlock + (int)threadIdx.x;
+    if (p >= P.n_store) return;
+    const uint32_t mask = P.mask[p];
+    if ((mask & kGhostBit) || ((mask >> kTypeShift) & 3u) != kBulk) return;
+    float nx = 0.0f, ny = 0.0f, nz = 0.0f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if ((mask >> opp(i)) & 1u) {  // y + c_i cannot pull from y: wall link
+            nx += L::w(i) * L::cx(i);
+            ny += L::w(i) * L::cy(i);
+            nz += L::w(i) * L::cz(i);
+        }
+    }
+    const float nn = sqrtf(nx * nx + ny * ny + nz * nz);
+    if (!(nn > 0.0f)) return;
+    nx /= nn;
+    ny /= nn;
+    nz /= nn;
+    const Coords c = coords_of(P, p);
+    float g[Q];
+    pull_general<Q, T>(P, static_cast<const T*>(P.fsrc), c, mask, g);
+    const Moments<Q> m = moments<Q>(g);
+    const Macro M = macroscopic(P, __ldg(P.phi + p), m.sd, m.mx, m.my, m.mz);
+    // corrected second moment Pi (as for the shear rate of the step)
+    const float sd3 = M.sd * (1.0f / 3.0f);
+    const float pxx = fmaf(M.ux, fmaf(-M.sigma, M.ux, M.Fx), m.sxx - sd3);
+    const float pyy = fmaf(M.uy, fmaf(-M.sigma, M.uy, M.Fy), m.syy - sd3);
+    const float pzz = fmaf(M.uz, fmaf(-M.sigma, M.uz, M.Fz), m.szz - sd3);
+    const float pxy = fmaf(M.ux, fmaf(-M.sigma, M.uy, 0.5f * M.Fy), fmaf(0.5f * M.Fx, M.uy, m.sxy));
+    const float pxz = fmaf(M.ux, fmaf(-M.sigma, M.uz, 0.5f * M.Fz), fmaf(0.5f * M.Fx, M.uz, m.sxz));
+    const float pyz = fmaf(M.uy, fmaf(-M.sigma, M.uz, 0.5f * M.Fz), fmaf(0.5f * M.Fy, M.uz, m.syz));
+    const float pn = sqrtf(fmaf(pxx, pxx, fmaf(pyy, pyy, fmaf(pzz, pzz, 2.0f * fmaf(pxy, pxy, fmaf(pxz, pxz, pyz * pyz))))));
+    const float gdot = 3.0f * P.omega[p] * pn / M.rho;
+    const float om = relaxation_rate(P, M.rho, gdot);
+    const float s = -(1.0f - 0.5f * om);
+    // sigma n, its normal part, and the tangential remainder
+    const float sx = s * fmaf(pxx, nx, fmaf(pxy, ny, pxz * nz));
+    const float sy = s * fmaf(pxy, nx, fmaf(pyy, ny, pyz * nz));
+    const float sz = s * fmaf(pxz, nx, fmaf(pyz, ny, pzz * nz));
+    const float sn = fmaf(sx, nx, fmaf(sy, ny, sz * nz));
+    const float tx = sx - sn * nx, ty = sy - sn * ny, tz = sz - sn * nz;
+    out[compact ? (long long)p : c.idx] = sqrtf(fmaf(tx, tx, fmaf(ty, ty, tz * tz)));
+}
+
+cudaError_t launch_wall_shear(int q, int storage, const Params& P, float* out, int compact, cudaStream_t s)
+{
+    const int grid = (P.n_store + kBlock - 1) / kBlock;
+    if (grid == 0) return cudaSuccess;
+    if (q == 19) {
+        if (storage == 0) wall_shear_kernel<19, float><<<grid, kBlock, 0, s>>>(P, out, compact);
+        else if (storage == 1) wall_shear_kernel<19, __half><<<grid, kBlock, 0, s>>>(P, out, compact);
+        else wall_shear_kernel<19, __nv_bfloat16><<<grid, kBlock, 0, s>>>(P, out, compact);
+    } else {
+        if (storage == 0) wall_shear_kernel<27, float><<<grid, kBlock, 0, s>>>(P, out, compact);
+        else if (storage == 1) wall_shear_kernel<27, __half><<<grid, kBlock, 0, s>>>(P, out, compact);
+        else wall_shear_kernel<27, __nv_bfloat16><<<grid, kBlock, 0, s>>>(P, out, compact);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

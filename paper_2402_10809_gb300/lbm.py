@@ -22,7 +22,7 @@ STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM
 SYMBOLS = ["lbm_list_length", "lbm_workspace_size", "lbm_init", "lbm_step", "lbm_moments", "lbm_diag", "lbm_diag_noalloc",
            "lbm_set_check",
            "lbm_state_size", "lbm_save", "lbm_load", "lbm_time", "lbm_fluid_count", "lbm_last_error",
-           "lbm_destroy", "lbm_adjoint_workspace_size", "lbm_adjoint"]
+           "lbm_destroy", "lbm_adjoint_workspace_size", "lbm_adjoint", "lbm_wall_shear"]
 
 
 class lbm_grid(C.Structure):
@@ -101,6 +101,8 @@ def load(build_if_missing=True):
     L.lbm_fluid_count.argtypes = [vp]
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_last_error.argtypes = [vp]
+    L.lbm_wall_shear.restype = C.c_int
+    L.lbm_wall_shear.argtypes = [vp, vp, C.c_int32]
     L.lbm_adjoint_workspace_size.restype = C.c_size_t
     L.lbm_adjoint_workspace_size.argtypes = [vp, C.c_int32, C.c_int32]
     L.lbm_adjoint.restype = C.c_int
@@ -188,6 +190,10 @@ def lbm_diag_noalloc(ctx, region_device):
     out = (C.c_double * 8)()
     _check(ctx, load().lbm_diag_noalloc(ctx, C.c_void_p(region_device), out))
     return np.array(out[:], dtype=np.float64)
+
+
+def lbm_wall_shear(ctx, wss, dst_on_device):
+    _check(ctx, load().lbm_wall_shear(ctx, C.c_void_p(wss), int(dst_on_device)))
 
 
 def lbm_set_check(ctx, check_every):
@@ -312,6 +318,16 @@ class Simulation:
         om = np.zeros(self.shape, np.float32)
         lbm_moments(self.ctx, rho.ctypes.data, u.ctypes.data, g.ctypes.data, om.ctypes.data, 0)
         return dict(rho=rho, u=u, gdot=g, omega=om)
+
+    def wall_shear(self, on_device=False):
+        """Voxel wall-shear-stress proxy |tau| of the current time on the dense box."""
+        if on_device:
+            out = self.torch.empty(self.shape, dtype=self.torch.float32, device=self.device)
+            lbm_wall_shear(self.ctx, out.data_ptr(), 1)
+            return out
+        out = np.zeros(self.shape, np.float32)
+        lbm_wall_shear(self.ctx, out.ctypes.data, 0)
+        return out
 
     def diag(self, region=None):
         if region is None:
