@@ -404,12 +404,21 @@ def coil_study(torch, lbm, args):
     pulsatile inflow.  Throughput from CUDA events around the time steps (the
     diagnostic launches are outside the timed chunks); the sac-mean |u| over
     the fluid cells of the sac and over its whole volume (wire voxels count as
-    u = 0), averaged over the last 1000 steps, and their reduction relative to
-    the uncoiled case."""
+    u = 0), and the mean wall shear stress (lbm_wall_shear) over the sac wall —
+    the fluid cells of the sac next to the vessel wall of the uncoiled geometry,
+    so that the coil's own surface is left out — each averaged over the last
+    1000 steps, and their change relative to the uncoiled case."""
     from lbm_inputs import aneurysm_problem, coil_problem, wire_coil
 
     n, steps, every, last = args.coil_n, args.coil_steps, 100, 1000
     wire = wire_coil(n)
+    from scipy.ndimage import binary_dilation
+
+    plain = aneurysm_problem(n, porous_sac=False)
+    sac_wall = (plain.region > 0) & (plain.flags > 0) & binary_dilation(plain.flags == 0, np.ones((3, 3, 3), bool))
+    sac_wall_t = torch.from_numpy(sac_wall).to("cuda")
+    del plain
+    wss = torch.empty(sac_wall.shape, dtype=torch.float32, device="cuda")
     cases = [("uncoiled", lambda: aneurysm_problem(n, porous_sac=False)),
              ("resolved", lambda: coil_problem(n, True, wire=wire)),
              ("averaged", lambda: coil_problem(n, False, wire=wire))]
@@ -420,7 +429,8 @@ def coil_study(torch, lbm, args):
         prob = make()
         sim = lbm.Simulation(prob)
         sim.step(every)  # warm-up chunk, not timed
-        t_run, u_sum, v_sum, k, bad = 0.0, 0.0, 0.0, 0, 0.0
+        t_run, u_sum, v_sum, w_sum, k, bad = 0.0, 0.0, 0.0, 0.0, 0, 0.0
+        wall = sac_wall_t & torch.from_numpy(prob.flags > 0).to("cuda")
         n_region = float((prob.region > 0).sum())
         for _ in range(steps // every - 1):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -434,18 +444,22 @@ def coil_study(torch, lbm, args):
                 d = sim.diag(prob.region)
                 u_sum += d[2] / max(d[3], 1.0)
                 v_sum += d[2] / n_region
+                lbm.lbm_wall_shear(sim.ctx, wss.data_ptr(), 1)
+                w_sum += float(wss[wall].mean().item())
                 bad = max(bad, d[7])
                 k += 1
         timed_steps = (steps // every - 1) * every
         res[name] = {"fluid_cells": int(prob.n_fluid), "value": float(prob.n_fluid * timed_steps / t_run / 1e6),
                      "unit": UNIT, "sac_mean_u": float(u_sum / max(k, 1)),
-                     "sac_volume_mean_u": float(v_sum / max(k, 1)), "finite": bool(bad == 0)}
+                     "sac_volume_mean_u": float(v_sum / max(k, 1)),
+                     "sac_wall_mean_wss": float(w_sum / max(k, 1)), "sac_wall_cells": int(wall.sum().item()),
+                     "finite": bool(bad == 0)}
         if name != "uncoiled":
             res[name]["min_porosity"] = float(prob.phi[prob.flags > 0].min())
         sim.close()
         del sim, prob
     for name in ("resolved", "averaged"):
-        for key in ("sac_mean_u", "sac_volume_mean_u"):
+        for key in ("sac_mean_u", "sac_volume_mean_u", "sac_wall_mean_wss"):
             res[name][key + "_reduction"] = 1.0 - res[name][key] / res["uncoiled"][key]
     return res
 
