@@ -352,7 +352,7 @@ def adjoint_cost(torch, lbm, args):
             res[name] = {"K": k, "skipped": f"needs {nbytes / 1e9:.1f} GB"}
             continue
         ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-        run = lambda: lbm.lbm_adjoint(sim.ctx, T, k, reg.ctypes.data, 0, ws.data_ptr(), nbytes, grad.data_ptr())
+        run = lambda: lbm.lbm_adjoint(sim.ctx, T, k, 0, reg.ctypes.data, 0, ws.data_ptr(), nbytes, grad.data_ptr())
         run()
         t_adj, J = timed(run, 3)
         res[name] = {"K": k, "seconds": t_adj, "cost_vs_forward": t_adj / t_fwd, "J": J,

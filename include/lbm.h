@@ -201,16 +201,20 @@ lbm_status lbm_set_check(lbm_ctx* ctx, int32_t check_every);
  *   in the storage type plus min(K, T) dense FP32 density fields plus two FP32
  *   adjoint states.  K >= T keeps the whole trajectory (no replay).
  * lbm_adjoint:
+ *   objective 0: the kinetic-energy objective above; 1: the same time mean of
+ *            the wall-shear-stress proxy |tau| of lbm_wall_shear, averaged over
+ *            the cells of R with wall links (the sac-wall average of Sec. 4);
  *   region   [N] uint8, host or device memory (region_on_device);
  *   workspace / workspace_bytes: caller-owned device memory, 256-byte aligned;
  *   grad     [N] FP64 device memory, overwritten with dJ/dphi (0 on solid
  *            cells); the accumulation over time steps is in FP64;
  *   J        host double, the objective value.
  * Synchronises the context's stream.  LBM_EINVAL on bad arguments or a region
- * without fluid cells, LBM_ENOMEM when the workspace is too small. */
+ * without fluid cells (for objective 1: without wall cells), LBM_ENOMEM when
+ * the workspace is too small. */
 size_t lbm_adjoint_workspace_size(const lbm_ctx* ctx, int32_t T, int32_t K);
-lbm_status lbm_adjoint(lbm_ctx* ctx, int32_t T, int32_t K, const uint8_t* region, int32_t region_on_device,
-                       void* workspace, size_t workspace_bytes, double* grad, double* J);
+lbm_status lbm_adjoint(lbm_ctx* ctx, int32_t T, int32_t K, int32_t objective, const uint8_t* region,
+                       int32_t region_on_device, void* workspace, size_t workspace_bytes, double* grad, double* J);
 
 /* Checkpoint of the full state (distributions, relaxation rates, time): size in
  * bytes, save into / load from caller memory (host or device). */

@@ -314,17 +314,52 @@ class TorchLBM:
         return dict(rho=torch.where(fl, rho, z), u=torch.where(fl, u, torch.zeros_like(u)),
                     gdot=torch.where(fl, gdot, z), omega=torch.where(fl, om, z))
 
-    def objective(self, phi, T, region, checkpoint=True):
-        """J = (1/T) sum_{t=1..T} mean over the region of rho |u|^2 / 2."""
+    def wall_normal(self):
+        """Voxel wall direction of every plain fluid cell: the normalised sum of
+        w_i c_i over its links to solid cells or out of the box (zero where
+        there are none); and the mask of cells that have such links."""
+        walls = torch.stack([~self.dest_fluid[i] for i in range(self.Q)]).to(torch.float64)
+        n = torch.einsum("q...,qa->a...", walls * self.w, self.cf)
+        nn = torch.sqrt((n * n).sum(0))
+        has = (nn > 1e-12) & (self.flags == FLUID)
+        return torch.where(has, n / torch.where(has, nn, torch.ones_like(nn)), torch.zeros_like(n)), has
+
+    def wall_shear(self, f, omega_prev, phi):
+        """Voxel wall-shear-stress proxy |tau| of state f: tau = sigma n -
+        (n . sigma n) n, sigma = -(1 - omega/2) Pi with the corrected second
+        moment Pi of the shear rate and omega of the collision of this time."""
+        rho, u, F = self.macroscopic(f, phi)
+        feq = self.equilibrium(phi, rho, u)
+        d = f - feq
+        P = torch.einsum("qa,qb,q...->ab...", self.cf, self.cf, d)
+        P = P + 0.5 * (F.unsqueeze(1) * u.unsqueeze(0) + u.unsqueeze(1) * F.unsqueeze(0))
+        nrm = _safe_norm((P * P).sum((0, 1)))
+        gdot = omega_prev * nrm / (CS2 * rho)
+        om = self.rate(rho, self.viscosity(gdot))
+        n, has = self.wall_normal()
+        sn = -(1 - om / 2) * torch.einsum("ab...,b...->a...", P, n)
+        tau = sn - (sn * n).sum(0) * n
+        return torch.where(has, _safe_norm((tau * tau).sum(0)), torch.zeros_like(rho))
+
+    def objective(self, phi, T, region, checkpoint=True, kind="ke"):
+        """J = (1/T) sum_{t=1..T} of the region mean of rho |u|^2 / 2
+        (kind "ke"), or of |tau| over the region's cells with wall links
+        (kind "wss")."""
         reg = torch.as_tensor(region.astype(bool)) & self.fluid
+        if kind == "wss":
+            reg = reg & self.wall_normal()[1]
         cnt = float(reg.sum())
         f, om = self.initial(phi)
         J = torch.zeros((), dtype=torch.float64)
 
         def one(f, om, t):
             f2, om2 = self.step(f, om, phi, t)
-            rho, u, _ = self.macroscopic(f2, phi)
-            ke = torch.where(reg, 0.5 * rho * (u * u).sum(0), torch.zeros_like(rho)).sum() / cnt
+            if kind == "wss":
+                val = self.wall_shear(f2, om2, phi)
+            else:
+                rho, u, _ = self.macroscopic(f2, phi)
+                val = 0.5 * rho * (u * u).sum(0)
+            ke = torch.where(reg, val, torch.zeros_like(val)).sum() / cnt
             return f2, om2, ke
 
         for t in range(T):
@@ -336,8 +371,8 @@ class TorchLBM:
             J = J + ke
         return J / T
 
-    def gradient(self, phi_np, T, region):
+    def gradient(self, phi_np, T, region, kind="ke"):
         phi = torch.tensor(np.asarray(phi_np, dtype=np.float64), requires_grad=True)
-        J = self.objective(phi, T, region)
+        J = self.objective(phi, T, region, kind=kind)
         J.backward()
         return float(J.detach()), phi.grad.detach().numpy()

@@ -8,7 +8,9 @@
 // pre-collision populations of time t (S(t-1) pulled, boundary conditions of
 // time t applied).  The objective is
 //     J = kappa sum_{t=1..T} sum_{y in R} rho(t, y) |u(t, y)|^2 / 2,
-// kappa = 1 / (T |R|), with rho and u from f(t) as in the collision of time t.
+// kappa = 1 / (T |R|), with rho and u from f(t) as in the collision of time t,
+// or (obj_kind 1) the same time-and-region mean of the wall-shear-stress proxy
+// |tau(t, y)| of lbm_wall_shear over the cells of R with wall links.
 // The adjoint states are lambda(t) = dJ/dS(t) (FP32, same [Q][n_store] layout) and
 // mu(t) = dJ/domega(t) (per slot).
 //
@@ -39,6 +41,7 @@ struct AdjParams {
     double* gphi;           // [n_store] dJ/dphi, accumulated
     const uint8_t* region;  // dense objective region R
     float kappa;            // 1 / (T |R|)
+    int obj_kind;           // 0: rho |u|^2 / 2 over R; 1: wall-shear-stress proxy |tau| over R's wall cells
     int first;              // t = T: no collision of time t in the objective's history
     int objective;          // t >= 1: the kinetic-energy term of time t belongs to J
     int last;               // t = 0: S(-1) and omega(-1) are constants
@@ -391,6 +394,47 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     const float iE = __fdividef(1.0f, E);
     const float om = 2.0f * M.rho * iE;
 
+    // wall-shear-stress objective at a wall cell of the region: |tau| =
+    // (1 - omega/2) |v|, v = (I - n n^T) Pi n; its seeds for omega and for the
+    // symmetric adjoint of Pi, (1 - omega/2) (t n^T + n t^T) / 2 with t = v / |v|
+    float w_om = 0.0f, wxx = 0.0f, wyy = 0.0f, wzz = 0.0f, wxy = 0.0f, wxz = 0.0f, wyz = 0.0f;
+    if (A.objective && A.obj_kind == 1 && type == kBulk &&
+        A.region[fast ? (long long)x + (long long)P.nx * row : cg.idx]) {
+        float nx = 0.0f, ny = 0.0f, nz = 0.0f;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if ((mask >> opp(i)) & 1u) {
+                nx += L::w(i) * L::cx(i);
+                ny += L::w(i) * L::cy(i);
+                nz += L::w(i) * L::cz(i);
+            }
+        }
+        const float nn = sqrtf(nx * nx + ny * ny + nz * nz);
+        if (nn > 0.0f) {
+            nx /= nn;
+            ny /= nn;
+            nz /= nn;
+            const float qx = fmaf(pxx, nx, fmaf(pxy, ny, pxz * nz));
+            const float qy = fmaf(pxy, nx, fmaf(pyy, ny, pyz * nz));
+            const float qz = fmaf(pxz, nx, fmaf(pyz, ny, pzz * nz));
+            const float qn = fmaf(qx, nx, fmaf(qy, ny, qz * nz));
+            const float vx = qx - qn * nx, vy = qy - qn * ny, vz = qz - qn * nz;
+            const float vn = sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
+            const float h2 = fmaf(-0.5f, om, 1.0f);
+            jv += (double)A.kappa * (double)(h2 * vn);
+            w_om = -0.5f * A.kappa * vn;
+            if (vn > 0.0f) {
+                const float k = A.kappa * h2 / vn;
+                wxx = k * vx * nx;
+                wyy = k * vy * ny;
+                wzz = k * vz * nz;
+                wxy = 0.5f * k * fmaf(vx, ny, vy * nx);
+                wxz = 0.5f * k * fmaf(vx, nz, vz * nx);
+                wyz = 0.5f * k * fmaf(vy, nz, vz * ny);
+            }
+        }
+    }
+
     // ---- reverse of the collision: out_i = (1 - omega) g_i
     //      + w_i [omega (sd + sigma pe_i) + (1 - omega/2) q_i] + w_i (rho - 1)(phi_i - phi),
     // pe_i = 3 c.u + 4.5 (c.u)^2 - 1.5 u.u, q_i = 3 c.F - 3 u.F + 9 (c.u)(c.F).
@@ -450,6 +494,7 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
         b.Fz = h2 * Buz;
         phib = -M.drho * Wd;
     }
+    omb += w_om;
     // omega = 2 rho / (6 mu + rho)
     b.rho = omb * 12.0f * mu * iE * iE;
     const float mub = -omb * 12.0f * M.rho * iE * iE;
@@ -463,7 +508,7 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     const float pnb = gdb * 3.0f * om_prev * irho;
     b.rho -= gdb * gdot * irho;
     // objective term of time t
-    if (A.objective && A.region[fast ? (long long)x + (long long)P.nx * row : cg.idx]) {
+    if (A.objective && A.obj_kind == 0 && A.region[fast ? (long long)x + (long long)P.nx * row : cg.idx]) {
         const float uu = fmaf(M.ux, M.ux, fmaf(M.uy, M.uy, M.uz * M.uz));
         jv += (double)A.kappa * 0.5 * (double)M.rho * (double)uu;
         b.rho = fmaf(0.5f * A.kappa, uu, b.rho);
@@ -474,7 +519,8 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     }
     // Pi = S - (sd/3) I - sigma u u^T + (F u^T + u F^T) / 2, |Pi| its Frobenius norm
     const float s = pn > 0.0f ? __fdividef(pnb, pn) : 0.0f;
-    const float bxx = s * pxx, byy = s * pyy, bzz = s * pzz, bxy = s * pxy, bxz = s * pxz, byz = s * pyz;
+    const float bxx = fmaf(s, pxx, wxx), byy = fmaf(s, pyy, wyy), bzz = fmaf(s, pzz, wzz);
+    const float bxy = fmaf(s, pxy, wxy), bxz = fmaf(s, pxz, wxz), byz = fmaf(s, pyz, wyz);
     {
         const float Pux = fmaf(bxx, M.ux, fmaf(bxy, M.uy, bxz * M.uz));
         const float Puy = fmaf(bxy, M.ux, fmaf(byy, M.uy, byz * M.uz));

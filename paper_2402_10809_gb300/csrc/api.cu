@@ -727,12 +727,14 @@ extern "C" size_t lbm_adjoint_workspace_size(const lbm_ctx* c, int32_t T, int32_
     return adj_layout(c, T, K).end;
 }
 
-extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, const uint8_t* region, int32_t region_on_device,
-                                  void* workspace, size_t workspace_bytes, double* grad, double* J)
+extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, int32_t objective, const uint8_t* region,
+                                  int32_t region_on_device, void* workspace, size_t workspace_bytes, double* grad,
+                                  double* J)
 {
     if (!c) return LBM_EINVAL;
     if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
     if (T < 1 || K < 1) return fail(c, LBM_EINVAL, "T and K must be >= 1");
+    if (objective != 0 && objective != 1) return fail(c, LBM_EINVAL, "objective must be 0 (kinetic energy) or 1 (wall shear)");
     if (!region || !workspace || !grad || !J) return fail(c, LBM_EINVAL, "null pointer argument");
     if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
         return fail(c, LBM_EINVAL, "adjoint workspace not 256-byte aligned");
@@ -763,10 +765,15 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, const uint8_
                  "copy outlet slots");
     unsigned long long* cnt_dev = reinterpret_cast<unsigned long long*>(w + AL.count);
     unsigned long long cnt = 0;
-    LBM_CUDA(launch_region_count(B.rows, B.rowbase, B.mask, c->n_store, c->grid.nx, reg, cnt_dev, st), "region count");
+    // objective 1 averages over the region's plain fluid cells with a wall link
+    const uint32_t wall_bits = objective == 1 ? ((1u << c->grid.q) - 2u) : 0u;
+    LBM_CUDA(launch_region_count(B.rows, B.rowbase, B.mask, c->n_store, c->grid.nx, reg, wall_bits, cnt_dev, st),
+             "region count");
     LBM_CUDA(cudaMemcpyAsync(&cnt, cnt_dev, sizeof(cnt), cudaMemcpyDeviceToHost, st), "copy region count");
     LBM_CUDA(cudaStreamSynchronize(st), "region count sync");
-    if (cnt == 0) return fail(c, LBM_EINVAL, "the objective region holds no fluid cell");
+    if (cnt == 0)
+        return fail(c, LBM_EINVAL, objective == 1 ? "the objective region holds no fluid cell next to a wall"
+                                                  : "the objective region holds no fluid cell");
     const int nblk = total_blocks(B);
     LBM_CUDA(cudaMemsetAsync(grad, 0, N * 8, st), "clear gradient");
     LBM_CUDA(cudaMemsetAsync(gphi, 0, n * 8, st), "clear packed gradient");
@@ -823,6 +830,7 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, const uint8_
     A.gphi = gphi;
     A.region = reg;
     A.kappa = (float)(1.0 / ((double)T * (double)cnt));
+    A.obj_kind = objective;
     A.out_slots = outs;
     A.out_ord = reinterpret_cast<uint32_t*>(w + AL.ord);
     A.n_out = c->n_out;

@@ -240,16 +240,19 @@ __global__ void fill_f32(float* p, long long n, float v)
     if (i < n) p[i] = v;
 }
 
-// Number of non-ghost slots whose region byte (dense) is set.
+// Number of non-ghost slots whose region byte (dense) is set; with wall_bits
+// nonzero only plain fluid cells with a wall link (mask & wall_bits) count.
 __global__ void region_count(const uint32_t* __restrict__ rows, const int* __restrict__ rowbase,
                              const uint32_t* __restrict__ mask, int n_store, int nx, const uint8_t* __restrict__ region,
-                             unsigned long long* out)
+                             uint32_t wall_bits, unsigned long long* out)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     int hit = 0;
     if (p < n_store && !(mask[p] & kGhostBit)) {
+        const uint32_t m = mask[p];
+        const bool ok = !wall_bits || ((m & wall_bits) && ((m >> kTypeShift) & 3u) == kBulk);
         const uint32_t r = rows[p];
-        hit = region[(long long)(p - rowbase[r]) + (long long)nx * r] ? 1 : 0;
+        hit = ok && region[(long long)(p - rowbase[r]) + (long long)nx * r] ? 1 : 0;
     }
     const unsigned int warp_hits = __popc(__ballot_sync(0xffffffffu, hit));
     if ((threadIdx.x & 31) == 0 && warp_hits) atomicAdd(out, (unsigned long long)warp_hits);
@@ -305,11 +308,11 @@ cudaError_t launch_fill_f32(float* p, long long n, float v, cudaStream_t s)
 }
 
 cudaError_t launch_region_count(const uint32_t* rows, const int* rowbase, const uint32_t* mask, int n_store, int nx,
-                                const uint8_t* region, unsigned long long* out, cudaStream_t s)
+                                const uint8_t* region, uint32_t wall_bits, unsigned long long* out, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess || n_store == 0) return e;
-    region_count<<<(n_store + 255) / 256, 256, 0, s>>>(rows, rowbase, mask, n_store, nx, region, out);
+    region_count<<<(n_store + 255) / 256, 256, 0, s>>>(rows, rowbase, mask, n_store, nx, region, wall_bits, out);
     return cudaGetLastError();
 }
 

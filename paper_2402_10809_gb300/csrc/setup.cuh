@@ -45,7 +45,7 @@ cudaError_t launch_setup_mask(int q, const SetupParams& S, cudaStream_t s);
 cudaError_t launch_diag_finish(const double* partials, int nblk, double* out, cudaStream_t s);
 cudaError_t launch_fill_f32(float* p, long long n, float v, cudaStream_t s);
 cudaError_t launch_region_count(const uint32_t* rows, const int* rowbase, const uint32_t* mask, int n_store, int nx,
-                                const uint8_t* region, unsigned long long* out, cudaStream_t s);
+                                const uint8_t* region, uint32_t wall_bits, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_scatter_f64(const uint32_t* rows, const int* rowbase, const uint32_t* mask, int n_store, int nx,
                                const double* src, double* dst, cudaStream_t s);
 

@@ -106,7 +106,7 @@ def load(build_if_missing=True):
     L.lbm_adjoint_workspace_size.restype = C.c_size_t
     L.lbm_adjoint_workspace_size.argtypes = [vp, C.c_int32, C.c_int32]
     L.lbm_adjoint.restype = C.c_int
-    L.lbm_adjoint.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, C.c_size_t, vp, P(C.c_double)]
+    L.lbm_adjoint.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, vp, C.c_int32, vp, C.c_size_t, vp, P(C.c_double)]
     L.lbm_destroy.restype = None
     L.lbm_destroy.argtypes = [vp]
     _lib = L
@@ -232,11 +232,14 @@ def lbm_adjoint_workspace_size(ctx, T, K):
     return int(load().lbm_adjoint_workspace_size(ctx, int(T), int(K)))
 
 
-def lbm_adjoint(ctx, T, K, region, region_on_device, workspace, workspace_bytes, grad):
-    """Runs the adjoint; grad is the device address of an FP64 [N] array.
-    Returns J."""
+OBJECTIVES = {"ke": 0, "wss": 1}
+
+
+def lbm_adjoint(ctx, T, K, objective, region, region_on_device, workspace, workspace_bytes, grad):
+    """Runs the adjoint (objective 0: sac kinetic energy, 1: sac-wall shear
+    stress); grad is the device address of an FP64 [N] array.  Returns J."""
     J = C.c_double(0.0)
-    _check(ctx, load().lbm_adjoint(ctx, int(T), int(K), C.c_void_p(region), int(region_on_device),
+    _check(ctx, load().lbm_adjoint(ctx, int(T), int(K), int(objective), C.c_void_p(region), int(region_on_device),
                                    C.c_void_p(workspace), C.c_size_t(workspace_bytes), C.c_void_p(grad),
                                    C.byref(J)))
     return float(J.value)
@@ -347,10 +350,12 @@ class Simulation:
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         lbm_load(self.ctx, buf.ctypes.data, buf.size, 0)
 
-    def adjoint(self, T, K, region):
-        """(J, dJ/dphi) of the sac kinetic-energy objective over steps 1..T
-        with a checkpoint every K steps; dJ/dphi is an FP64 device tensor
+    def adjoint(self, T, K, region, objective="ke"):
+        """(J, dJ/dphi) of the sac objective over steps 1..T with a checkpoint
+        every K steps: "ke" the mean kinetic energy, "wss" the mean wall shear
+        stress over the region's wall cells; dJ/dphi is an FP64 device tensor
         shaped like the box."""
+        kind = OBJECTIVES[objective]
         torch = self.torch
         nbytes = lbm_adjoint_workspace_size(self.ctx, T, K)
         if nbytes == 0:
@@ -359,10 +364,10 @@ class Simulation:
         grad = torch.empty(self.shape, dtype=torch.float64, device=self.device)
         if hasattr(region, "data_ptr"):
             reg = region.to(device=self.device, dtype=torch.uint8).contiguous()
-            J = lbm_adjoint(self.ctx, T, K, reg.data_ptr(), 1, ws.data_ptr(), nbytes, grad.data_ptr())
+            J = lbm_adjoint(self.ctx, T, K, kind, reg.data_ptr(), 1, ws.data_ptr(), nbytes, grad.data_ptr())
         else:
             reg = np.ascontiguousarray(region, dtype=np.uint8)
-            J = lbm_adjoint(self.ctx, T, K, reg.ctypes.data, 0, ws.data_ptr(), nbytes, grad.data_ptr())
+            J = lbm_adjoint(self.ctx, T, K, kind, reg.ctypes.data, 0, ws.data_ptr(), nbytes, grad.data_ptr())
         return J, grad
 
 
@@ -371,6 +376,17 @@ def sac_kinetic_energy(problem, phi, T, K, region, storage="f32"):
     differentiable torch function of the porosity tensor phi (any device; the
     computation runs on the current CUDA device).  Backward returns the
     gradient from the hand-written adjoint (lbm_adjoint)."""
+    return _sac_objective(problem, phi, T, K, region, storage, "ke")
+
+
+def sac_wall_shear(problem, phi, T, K, region, storage="f32"):
+    """J(phi) = time mean over steps 1..T of the wall-shear-stress proxy |tau|
+    averaged over the region's wall cells, as a differentiable torch function
+    of phi (backward: lbm_adjoint with objective 1)."""
+    return _sac_objective(problem, phi, T, K, region, storage, "wss")
+
+
+def _sac_objective(problem, phi, T, K, region, storage, objective):
     import torch
 
     class _SacKE(torch.autograd.Function):
@@ -379,7 +395,7 @@ def sac_kinetic_energy(problem, phi, T, K, region, storage="f32"):
             prob = _with_porosity(problem, phi_t.detach().cpu().numpy())
             sim = Simulation(prob, storage=storage)
             try:
-                J, grad = sim.adjoint(T, K, region)
+                J, grad = sim.adjoint(T, K, region, objective)
             finally:
                 sim.close()
             ctx.save_for_backward(grad.to(device=phi_t.device, dtype=phi_t.dtype))

@@ -167,8 +167,35 @@ def test_adjoint_rejects_bad_arguments(lbm):
     grad = torch.empty(prob.flags.shape, dtype=torch.float64, device="cuda")
     reg = np.ascontiguousarray(prob.region, dtype=np.uint8)
     with pytest.raises(lbm.LBMError) as e:
-        lbm.lbm_adjoint(sim.ctx, 5, 2, reg.ctypes.data, 0, ws.data_ptr(), nbytes - 256, grad.data_ptr())
+        lbm.lbm_adjoint(sim.ctx, 5, 2, 0, reg.ctypes.data, 0, ws.data_ptr(), nbytes - 256, grad.data_ptr())
     assert e.value.status == lbm.LBM_ENOMEM
     with pytest.raises(lbm.LBMError) as e:
-        lbm.lbm_adjoint(sim.ctx, 5, 2, reg.ctypes.data, 0, ws.data_ptr() + 8, nbytes - 256, grad.data_ptr())
+        lbm.lbm_adjoint(sim.ctx, 5, 2, 0, reg.ctypes.data, 0, ws.data_ptr() + 8, nbytes - 256, grad.data_ptr())
     assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LBMError) as e:  # no such objective
+        lbm.lbm_adjoint(sim.ctx, 5, 2, 2, reg.ctypes.data, 0, ws.data_ptr(), nbytes, grad.data_ptr())
+    assert e.value.status == lbm.LBM_EINVAL
+
+
+@pytest.mark.parametrize("q", [27, 19])
+def test_wall_shear_objective_matches_reference_gradient(lbm, q):
+    """Objective 1: time-and-sac-wall mean of the wall-shear-stress proxy,
+    against autograd of the torch restatement (whose proxy equals the C
+    oracle's, see test_oracle_crosscheck)."""
+    prob = aneurysm_problem(24, q=q, small=True, u0=0.05, period=50.0)
+    T = 40
+    Jr, gr = TorchLBM(prob).gradient(prob.phi, T, prob.region, kind="wss")
+    sim = lbm.Simulation(prob)
+    J, g = sim.adjoint(T, 8, prob.region, "wss")
+    g = g.cpu().numpy()
+    assert abs(J - Jr) <= TOL_J * abs(Jr), (J, Jr)
+    e = grad_err(g, gr)
+    assert e <= TOL_GRAD, e
+
+
+def test_wall_shear_objective_independent_of_checkpoint_interval(lbm):
+    prob = aneurysm_problem(24, q=27, small=True, u0=0.05, period=50.0)
+    sim = lbm.Simulation(prob)
+    J0, g0 = sim.adjoint(17, 17, prob.region, "wss")
+    J1, g1 = sim.adjoint(17, 3, prob.region, "wss")
+    assert J0 == J1 and np.array_equal(g0.cpu().numpy(), g1.cpu().numpy())

@@ -104,3 +104,39 @@ def test_reference_gradient_matches_finite_differences():
         jm = Oracle(prob, phi=ph).run_objective(T, prob.region)
         fd = (jp - jm) / (2 * eps)
         assert abs(fd - grad[z, y, x]) < 1e-4 * scale + 1e-6 * abs(fd)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_c_and_torch_wall_shear_agree(q):
+    """The voxel wall-shear-stress proxy of the two FP64 restatements."""
+    prob = aneurysm_problem(24, q=q, small=True, u0=0.05, period=100.0)
+    tl = TorchLBM(prob)
+    phi = torch.tensor(prob.phi.astype(np.float64))
+    f, om = tl.run(phi, 30)
+    wt = tl.wall_shear(f, om, phi).numpy()
+    o = Oracle(prob)
+    o.step(30)
+    wo = o.wall_shear()
+    assert np.array_equal(wt > 0, wo > 0)
+    assert np.abs(wt - wo).max() <= 1e-12 * np.abs(wo).max()
+
+
+def test_wall_shear_objective_gradient_matches_differences():
+    """Autograd of the torch wall-shear objective against its own central
+    differences (eps = 1e-5) at the two sac voxels of largest gradient, once
+    the inflow has reached the sac wall (T = 30)."""
+    prob = aneurysm_problem(24, q=19, small=True, u0=0.05, period=50.0)
+    T = 30
+    tl = TorchLBM(prob)
+    J, grad = tl.gradient(prob.phi, T, prob.region, kind="wss")
+    cand = np.argwhere((prob.region > 0) & (prob.flags > 0) & (prob.phi < 0.99) & (prob.phi > 0.61))
+    order = np.argsort(-np.abs(grad[tuple(cand.T)]))
+    scale = np.abs(grad).max()
+    for z, y, x in cand[order[:2]]:
+        vals = []
+        for sgn in (1, -1):
+            ph = prob.phi.astype(np.float64).copy()
+            ph[z, y, x] += sgn * 1e-5
+            vals.append(float(tl.objective(torch.tensor(ph), T, prob.region, checkpoint=False, kind="wss")))
+        fd = (vals[0] - vals[1]) / 2e-5
+        assert abs(fd - grad[z, y, x]) <= 1e-4 * scale, (fd, grad[z, y, x])
