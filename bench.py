@@ -396,42 +396,83 @@ def wall_shear_pass(torch, lbm, sim, prob, stream):
             "max_wss": float(out.max().item())}
 
 
-def coil_study(torch, lbm, args):
-    """The fully resolved vs volume-averaged coil at the largest size (Sec. 4):
-    the n^3 aneurysm without coil, with the seeded random-walk wire (2 voxels
-    thick, 25 % of the sac) as solid voxels, and with the same wire box-filtered
-    into porosity over the paper's averaging window (28^3 cells); FP32,
-    pulsatile inflow.  Throughput from CUDA events around the time steps (the
-    diagnostic launches are outside the timed chunks); the sac-mean |u| over
-    the fluid cells of the sac and over its whole volume (wire voxels count as
-    u = 0), and the mean wall shear stress (lbm_wall_shear) over the sac wall —
-    the fluid cells of the sac next to the vessel wall of the uncoiled geometry,
-    so that the coil's own surface is left out — each averaged over the last
-    1000 steps, and their change relative to the uncoiled case."""
-    from lbm_inputs import aneurysm_problem, coil_problem, wire_coil
+COIL_PACKINGS = (0.15, 0.20, 0.25)
 
-    n, steps, every, last = args.coil_n, args.coil_steps, 100, 1000
-    wire = wire_coil(n)
+
+def porosity_average_cost(torch, lbm, wire_t, flags_t, stream, reps=5):
+    """The volume averaging of a coil on the GPU (lbm_porosity_average, three
+    sliding-window passes) at the coil study's box: median CUDA-event time over
+    `reps` calls after 3 warm-up calls on the launching stream (wire, flags and
+    porosity together exceed L2).  Algorithmic bytes: wire + flags read, FP32
+    porosity written = 6 B per cell."""
+    from lbm_inputs import COIL_PHI_MIN, COIL_WINDOW
+
+    nz, ny, nx = wire_t.shape
+    nbytes = lbm.lbm_porosity_workspace_size(nx, ny, nz)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    phi = torch.empty(tuple(wire_t.shape), dtype=torch.float32, device="cuda")
+
+    def call():
+        lbm.lbm_porosity_average(nx, ny, nz, wire_t.data_ptr(), flags_t.data_ptr(), COIL_WINDOW, COIL_PHI_MIN,
+                                 phi.data_ptr(), ws.data_ptr(), nbytes, stream.cuda_stream)
+
+    for _ in range(3):
+        call()
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e3)
+    us = float(np.median(times))
+    alg = 6 * wire_t.numel()
+    peak, kind = load_peaks()
+    return {"cells": int(wire_t.numel()), "window": COIL_WINDOW, "us": us, "kernel_launches": 3,
+            "algorithmic_bytes": int(alg), "achieved_gbs": alg / us / 1e3, "peak_gbs": peak,
+            "roofline_frac": (alg / us / 1e3) / peak, "peak_kind": kind}
+
+
+def coil_study(torch, lbm, args):
+    """The fully resolved vs volume-averaged coil (Sec. 4) at the largest size:
+    the n^3 aneurysm without coil, then for each packing density of the paper
+    (15, 20, 25 % of the sac) a seeded random-walk wire (2 voxels thick; the
+    lower packings are the first part of the same walk) as solid voxels, and the
+    same wire averaged into porosity over the paper's window (28^3 cells) on the
+    GPU (lbm_porosity_average).  FP32, pulsatile inflow.  Throughput from CUDA
+    events around the time steps (the diagnostic launches are outside the timed
+    chunks); the sac-mean |u| over the fluid cells of the sac and over its whole
+    volume (wire voxels count as u = 0), and the mean wall shear stress
+    (lbm_wall_shear) over the sac wall (the fluid cells of the sac next to the
+    vessel wall of the uncoiled geometry, so that the coil's own surface is left
+    out), each averaged over the last 1000 steps; their ratios to the uncoiled
+    case and of averaged to resolved."""
     from scipy.ndimage import binary_dilation
 
-    plain = aneurysm_problem(n, porous_sac=False)
-    sac_wall = (plain.region > 0) & (plain.flags > 0) & binary_dilation(plain.flags == 0, np.ones((3, 3, 3), bool))
+    from lbm_inputs import COIL_PHI_MIN, COIL_WINDOW, aneurysm_problem, coil_packings, coil_problem
+
+    n, steps, every, last = args.coil_n, args.coil_steps, 100, 1000
+    base = aneurysm_problem(n, porous_sac=False)
+    wires = coil_packings(n, COIL_PACKINGS)
+    sac_wall = (base.region > 0) & (base.flags > 0) & binary_dilation(base.flags == 0, np.ones((3, 3, 3), bool))
     sac_wall_t = torch.from_numpy(sac_wall).to("cuda")
-    del plain
+    flags_t = torch.from_numpy(np.ascontiguousarray(base.flags)).to("cuda")
+    n_region = float((base.region > 0).sum())
     wss = torch.empty(sac_wall.shape, dtype=torch.float32, device="cuda")
-    cases = [("uncoiled", lambda: aneurysm_problem(n, porous_sac=False)),
-             ("resolved", lambda: coil_problem(n, True, wire=wire)),
-             ("averaged", lambda: coil_problem(n, False, wire=wire))]
     stream = torch.cuda.current_stream()
-    res = {"workload": f"aneurysm{n} D3Q27 FP32, {steps} pulsatile steps; wire coil 25 % of the sac",
+    res = {"workload": f"aneurysm{n} D3Q27 FP32, {steps} pulsatile steps; wire coils at "
+                       + "/".join(f"{round(100 * p)}" for p in COIL_PACKINGS)
+                       + f" % of the sac, fully resolved and volume averaged over {COIL_WINDOW}^3 cells",
            "steps": steps}
-    for name, make in cases:
-        prob = make()
+
+    def run(prob):
         sim = lbm.Simulation(prob)
         sim.step(every)  # warm-up chunk, not timed
         t_run, u_sum, v_sum, w_sum, k, bad = 0.0, 0.0, 0.0, 0.0, 0, 0.0
-        wall = sac_wall_t & torch.from_numpy(prob.flags > 0).to("cuda")
-        n_region = float((prob.region > 0).sum())
+        wall = sac_wall_t & (flags_t > 0) if prob.flags is base.flags else \
+            sac_wall_t & torch.from_numpy(prob.flags > 0).to("cuda")
         for _ in range(steps // every - 1):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -449,18 +490,30 @@ def coil_study(torch, lbm, args):
                 bad = max(bad, d[7])
                 k += 1
         timed_steps = (steps // every - 1) * every
-        res[name] = {"fluid_cells": int(prob.n_fluid), "value": float(prob.n_fluid * timed_steps / t_run / 1e6),
-                     "unit": UNIT, "sac_mean_u": float(u_sum / max(k, 1)),
-                     "sac_volume_mean_u": float(v_sum / max(k, 1)),
-                     "sac_wall_mean_wss": float(w_sum / max(k, 1)), "sac_wall_cells": int(wall.sum().item()),
-                     "finite": bool(bad == 0)}
-        if name != "uncoiled":
-            res[name]["min_porosity"] = float(prob.phi[prob.flags > 0].min())
+        n_fluid = sim.n_fluid
         sim.close()
-        del sim, prob
-    for name in ("resolved", "averaged"):
-        for key in ("sac_mean_u", "sac_volume_mean_u", "sac_wall_mean_wss"):
-            res[name][key + "_reduction"] = 1.0 - res[name][key] / res["uncoiled"][key]
+        return {"fluid_cells": int(n_fluid), "value": float(n_fluid * timed_steps / t_run / 1e6), "unit": UNIT,
+                "sac_mean_u": float(u_sum / max(k, 1)), "sac_volume_mean_u": float(v_sum / max(k, 1)),
+                "sac_wall_mean_wss": float(w_sum / max(k, 1)), "sac_wall_cells": int(wall.sum().item()),
+                "finite": bool(bad == 0)}
+
+    keys = ("sac_mean_u", "sac_volume_mean_u", "sac_wall_mean_wss")
+    res["uncoiled"] = run(base)
+    res["porosity_average"] = porosity_average_cost(
+        torch, lbm, torch.from_numpy(wires[max(COIL_PACKINGS)]).to("cuda"), flags_t, stream)
+    for p in COIL_PACKINGS:
+        wire_t = torch.from_numpy(wires[p]).to("cuda")
+        phi_t = lbm.porosity_average(wire_t, COIL_WINDOW, COIL_PHI_MIN, flags_t)
+        r = {"packing": p, "wire_voxels": int(wires[p].sum()),
+             "resolved": run(coil_problem(n, True, wire=wires[p], base=base)),
+             "averaged": run(coil_problem(n, False, phi=phi_t, base=base))}
+        r["averaged"]["min_porosity"] = float(phi_t[flags_t > 0].min().item())
+        for case in ("resolved", "averaged"):
+            for key in keys:
+                r[case][key + "_ratio"] = r[case][key] / res["uncoiled"][key]
+        r["averaged_over_resolved"] = {key: r["averaged"][key] / r["resolved"][key] for key in keys}
+        res[f"packing_{round(100 * p)}"] = r
+        del wire_t, phi_t
     return res
 
 

@@ -181,6 +181,35 @@ lbm_status lbm_wall_shear(lbm_ctx* ctx, float* wss, int32_t dst_on_device);
  *    them.  No state carries over from one call to the next. */
 lbm_status lbm_diag_noalloc(lbm_ctx* ctx, const uint8_t* region, double out[8]);
 
+/* Volume-averaged porosity of a voxelised coil, the input that lbm_init takes
+ * as the porosity of the averaged simulations (Sec. 4: the porosity field is
+ * the windowed convolution of the voxelised coil with a uniform averaging
+ * kernel; Table 1: averaging window 1.23 mm).  No context is involved: this
+ * runs before lbm_init.  For every cell x of the nx * ny * nz box:
+ *     count(x) = number of wire voxels v with x_a - lo <= v_a <= x_a + hi on
+ *                every axis a, lo = window / 2, hi = window - 1 - lo (cells
+ *                outside the box hold no wire);
+ *     phi(x)   = max(phi_min, (window^3 - count(x)) / window^3), the quotient
+ *                correctly rounded to FP32 (count and window^3 are exact
+ *                integers), and phi(x) = 1 where flags[x] == LBM_SOLID.
+ *  - wire:  [nz][ny][nx] uint8, nonzero = wire voxel; device memory.
+ *  - flags: [nz][ny][nx] uint8 (the flags of lbm_init) or NULL for no solid
+ *           override; device memory.
+ *  - phi:   [nz][ny][nx] float, written; device memory.
+ *  - workspace: caller-owned device scratch, 256-byte aligned, at least
+ *           lbm_porosity_workspace_size(nx, ny, nz) bytes (3 bytes per cell).
+ *  - cuda_stream: the stream the three passes run on (asynchronous).
+ * Limits: 1 <= nx <= 16384, window 1..255 (window^2 fits the 16-bit
+ * intermediate, window^3 < 2^24), 0 <= phi_min <= 1.  Returns LBM_EINVAL on
+ * bad sizes, window, phi_min, pointers or alignment, LBM_ENOMEM when the
+ * workspace is too small, LBM_ECUDA when a launch fails (there is no context,
+ * hence no lbm_last_error text).  lbm_porosity_workspace_size returns 0 for
+ * bad sizes. */
+size_t lbm_porosity_workspace_size(int32_t nx, int32_t ny, int32_t nz);
+lbm_status lbm_porosity_average(int32_t nx, int32_t ny, int32_t nz, const uint8_t* wire, const uint8_t* flags,
+                                int32_t window, float phi_min, float* phi, void* workspace, size_t workspace_bytes,
+                                void* cuda_stream);
+
 /* Every check_every steps of later lbm_step calls, run the non-finite count of
  * lbm_diag and return LBM_EUNSTABLE when it is nonzero (0 = never, default). */
 lbm_status lbm_set_check(lbm_ctx* ctx, int32_t check_every);

@@ -18,11 +18,13 @@ from .geometry import (  # noqa: F401
     channel_flags,
     periodic_box_flags,
 )
-from .porosity import plug_porosity, sac_random_porosity, wire_coil  # noqa: F401
+from .porosity import coil_packings, plug_porosity, sac_random_porosity, wire_coil, wire_coil_order  # noqa: F401
 from .configs import (  # noqa: F401
     Problem,
     pipe_problem,
     aneurysm_problem,
+    COIL_PHI_MIN,
+    COIL_WINDOW,
     coil_problem,
     channel_problem,
     periodic_box_problem,

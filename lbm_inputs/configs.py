@@ -105,33 +105,37 @@ def aneurysm_problem(n, q=27, seed=0, small=False, porous_sac=True, u0=0.05, amp
     return Problem(name, flags, phi, q, (0, 0, 0), rheo, porous, bc, region)
 
 
-def coil_problem(n, resolved, packing=0.25, seed=0, q=27, window=28, phi_min=0.05, wire=None, **kw):
+# The paper's porosity averaging window (Table 1: 1.23 mm, 28 cells at the
+# Table 1 spacing) and the lower clamp of the averaged porosity.  With an 8^3
+# window the 2-voxel wire gives porosities down to the clamp and the scheme
+# loses finiteness on the 512^3 workload.
+COIL_WINDOW = 28
+COIL_PHI_MIN = 0.05
+
+
+def coil_problem(n, resolved, packing=0.25, seed=0, q=27, wire=None, phi=None, base=None, **kw):
     """The aneurysm of :func:`aneurysm_problem` with a wire coil in the sac
     (Sec. 4): a seeded random-walk helical wire, 2 voxels thick, filling
     ``packing`` of the sac (:func:`porosity.wire_coil`).
 
     ``resolved``: the wire voxels are solid (half-way bounce-back), porosity 1
     elsewhere.  Otherwise (volume averaged): every cell stays fluid and the
-    porosity is 1 minus the wire fraction in the ``window``^3 box around the
-    cell, clamped at ``phi_min``.  The default window is the paper's porosity
-    averaging window (Table 1: 1.23 mm, 28 cells at the Table 1 spacing); with
-    8^3 the 2-voxel wire gives porosities down to the clamp and the scheme
-    loses finiteness on the 512^3 workload.  ``wire``: a precomputed wire mask (else it
-    is generated from ``packing`` and ``seed``).  Other keywords go to
-    aneurysm_problem.
+    porosity is ``phi``, the volume average of the wire over the
+    COIL_WINDOW^3 box clamped at COIL_PHI_MIN, which the caller computes
+    (lbm.porosity_average on the GPU; the oracle's porosity_average in tests);
+    it may be a CUDA tensor.  ``wire``: a precomputed wire mask (else it is
+    generated from ``packing`` and ``seed``).  ``base``: the uncoiled problem,
+    if already built.  Other keywords go to aneurysm_problem.
     """
-    from scipy.ndimage import uniform_filter
-
-    base = aneurysm_problem(n, q=q, porous_sac=False, **kw)
+    base = base if base is not None else aneurysm_problem(n, q=q, porous_sac=False, **kw)
+    if not resolved:
+        if phi is None:
+            raise ValueError("the averaged coil takes its averaged porosity field as phi")
+        return dataclasses.replace(base, name=f"coil{n}a", phi=phi)
     wire = (por.wire_coil(n, packing=packing, seed=seed) if wire is None else wire) > 0
-    if resolved:
-        flags = base.flags.copy()
-        flags[wire] = 0
-        return dataclasses.replace(base, name=f"coil{n}r", flags=flags)
-    frac = uniform_filter(wire.astype(np.float32), size=window, mode="constant")
-    phi = np.clip(1.0 - frac, phi_min, 1.0).astype(np.float32)
-    phi[base.flags == 0] = 1.0
-    return dataclasses.replace(base, name=f"coil{n}a", phi=phi)
+    flags = base.flags.copy()
+    flags[wire] = 0
+    return dataclasses.replace(base, name=f"coil{n}r", flags=flags)
 
 
 def lattice_rheology(mu0, mu_inf, lam, n, a):

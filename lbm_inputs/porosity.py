@@ -53,10 +53,25 @@ def wire_coil(n, packing=0.25, seed=0, thickness_radius=1, small=False):
     ``thickness_radius`` (a 2-voxel-thick wire for radius 1).  Returns a uint8
     mask of wire voxels (inside the sac only).
     """
+    return (wire_coil_order(n, packing, seed, thickness_radius, small) >= 0).astype(np.uint8)
+
+
+def coil_packings(n, packings, seed=0, thickness_radius=1, small=False):
+    """Wires of several packing densities from one walk, the way a coil is
+    inserted: the wire of packing p is the first p |sac| voxels the walk of the
+    largest packing deposits.  Returns {p: uint8 mask}."""
+    order = wire_coil_order(n, max(packings), seed, thickness_radius, small)
+    n_sac = int((geo.sac_mask(n, small) > 0).sum())
+    return {p: ((order >= 0) & (order < int(p * n_sac))).astype(np.uint8) for p in packings}
+
+
+def wire_coil_order(n, packing=0.25, seed=0, thickness_radius=1, small=False):
+    """The walk of :func:`wire_coil`; returns an int32 array holding the
+    deposition index of every wire voxel and -1 elsewhere."""
     sc, r_s = geo.sac_sphere(n, small)
     sac = geo.sac_mask(n, small) > 0
     target = int(packing * sac.sum())
-    wire = np.zeros_like(sac)
+    wire = np.full(sac.shape, -1, dtype=np.int32)
     rng = np.random.default_rng(seed)
     p = np.array(sc, dtype=np.float64)
     d = rng.standard_normal(3)
@@ -89,7 +104,7 @@ def wire_coil(n, packing=0.25, seed=0, thickness_radius=1, small=False):
         ix, iy, iz = (int(np.floor(c)) for c in p)
         for dz, dy, dx in offs:
             z, y, x = iz + dz, iy + dy, ix + dx
-            if 0 <= x < n and 0 <= y < n and 0 <= z < n and sac[z, y, x] and not wire[z, y, x]:
-                wire[z, y, x] = True
+            if 0 <= x < n and 0 <= y < n and 0 <= z < n and sac[z, y, x] and wire[z, y, x] < 0:
+                wire[z, y, x] = count
                 count += 1
-    return wire.astype(np.uint8)
+    return wire

@@ -575,6 +575,34 @@ extern "C" lbm_status lbm_wall_shear(lbm_ctx* c, float* wss, int32_t dst_on_devi
     return LBM_OK;
 }
 
+static bool porosity_dims_ok(int32_t nx, int32_t ny, int32_t nz)
+{
+    return nx >= 1 && ny >= 1 && nz >= 1 && nx <= kPorosityMaxNx && (long long)nx * ny * nz <= (1ll << 40);
+}
+
+extern "C" size_t lbm_porosity_workspace_size(int32_t nx, int32_t ny, int32_t nz)
+{
+    if (!porosity_dims_ok(nx, ny, nz)) return 0;
+    const size_t N = (size_t)nx * ny * nz;
+    return align256(N) + align256(2 * N);
+}
+
+extern "C" lbm_status lbm_porosity_average(int32_t nx, int32_t ny, int32_t nz, const uint8_t* wire,
+                                           const uint8_t* flags, int32_t window, float phi_min, float* phi,
+                                           void* workspace, size_t workspace_bytes, void* cuda_stream)
+{
+    if (!porosity_dims_ok(nx, ny, nz) || !wire || !phi || !workspace) return LBM_EINVAL;
+    if (window < 1 || window > kPorosityMaxWindow || !(phi_min >= 0.0f && phi_min <= 1.0f)) return LBM_EINVAL;
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return LBM_EINVAL;
+    if (workspace_bytes < lbm_porosity_workspace_size(nx, ny, nz)) return LBM_ENOMEM;
+    const size_t N = (size_t)nx * ny * nz;
+    uint8_t* ws_x = static_cast<uint8_t*>(workspace);
+    uint16_t* ws_y = reinterpret_cast<uint16_t*>(ws_x + align256(N));
+    const cudaError_t e = launch_porosity_average(wire, flags, nx, ny, nz, window, phi_min, phi, ws_x, ws_y,
+                                                  static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
 extern "C" lbm_status lbm_set_check(lbm_ctx* c, int32_t check_every)
 {
     if (!c) return LBM_EINVAL;

@@ -49,4 +49,14 @@ cudaError_t launch_region_count(const uint32_t* rows, const int* rowbase, const 
 cudaError_t launch_scatter_f64(const uint32_t* rows, const int* rowbase, const uint32_t* mask, int n_store, int nx,
                                const double* src, double* dst, cudaStream_t s);
 
+// Volume-averaged porosity of a wire mask (porosity.cu): three sliding-window
+// passes through the caller's scratch (ws_x: N bytes, ws_y: N uint16).  The x
+// pass stages up to kPorosityRowBytes of rows per block in shared memory.
+constexpr int kPorosityRowBytes = 16384;
+constexpr int kPorosityMaxNx = 16384;
+constexpr int kPorosityMaxWindow = 255;  // window^2 fits uint16, window^3 < 2^24
+size_t porosity_smem_bytes(int nx);
+cudaError_t launch_porosity_average(const uint8_t* wire, const uint8_t* flags, int nx, int ny, int nz, int window,
+                                    float phi_min, float* phi, uint8_t* ws_x, uint16_t* ws_y, cudaStream_t s);
+
 }  // namespace lbm

@@ -22,7 +22,8 @@ STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM
 SYMBOLS = ["lbm_list_length", "lbm_workspace_size", "lbm_init", "lbm_step", "lbm_moments", "lbm_diag", "lbm_diag_noalloc",
            "lbm_set_check",
            "lbm_state_size", "lbm_save", "lbm_load", "lbm_time", "lbm_fluid_count", "lbm_last_error",
-           "lbm_destroy", "lbm_adjoint_workspace_size", "lbm_adjoint", "lbm_wall_shear"]
+           "lbm_destroy", "lbm_adjoint_workspace_size", "lbm_adjoint", "lbm_wall_shear",
+           "lbm_porosity_workspace_size", "lbm_porosity_average"]
 
 
 class lbm_grid(C.Structure):
@@ -107,6 +108,11 @@ def load(build_if_missing=True):
     L.lbm_adjoint_workspace_size.argtypes = [vp, C.c_int32, C.c_int32]
     L.lbm_adjoint.restype = C.c_int
     L.lbm_adjoint.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, vp, C.c_int32, vp, C.c_size_t, vp, P(C.c_double)]
+    L.lbm_porosity_workspace_size.restype = C.c_size_t
+    L.lbm_porosity_workspace_size.argtypes = [C.c_int32, C.c_int32, C.c_int32]
+    L.lbm_porosity_average.restype = C.c_int
+    L.lbm_porosity_average.argtypes = [C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_int32, C.c_float, vp, vp,
+                                       C.c_size_t, vp]
     L.lbm_destroy.restype = None
     L.lbm_destroy.argtypes = [vp]
     _lib = L
@@ -245,6 +251,43 @@ def lbm_adjoint(ctx, T, K, objective, region, region_on_device, workspace, works
     return float(J.value)
 
 
+def lbm_porosity_workspace_size(nx, ny, nz):
+    return int(load().lbm_porosity_workspace_size(int(nx), int(ny), int(nz)))
+
+
+def lbm_porosity_average(nx, ny, nz, wire, flags, window, phi_min, phi, workspace, workspace_bytes, stream):
+    """Device addresses (ints; flags may be 0); asynchronous on ``stream``."""
+    st = load().lbm_porosity_average(int(nx), int(ny), int(nz), C.c_void_p(wire), C.c_void_p(flags or None),
+                                     int(window), C.c_float(phi_min), C.c_void_p(phi), C.c_void_p(workspace),
+                                     C.c_size_t(workspace_bytes), C.c_void_p(stream))
+    if st != LBM_OK:
+        raise LBMError(st, "lbm_porosity_average")
+
+
+def porosity_average(wire, window, phi_min, flags=None, stream=None):
+    """Volume-averaged porosity of a wire mask: ``wire`` (and ``flags``) are
+    uint8 CUDA tensors of shape (nz, ny, nx); returns a float32 CUDA tensor."""
+    import torch
+
+    if wire.dtype != torch.uint8 or not wire.is_cuda or wire.dim() != 3:
+        raise ValueError("wire must be a 3-d uint8 CUDA tensor")
+    wire = wire.contiguous()
+    nz, ny, nx = wire.shape
+    if flags is not None:
+        if flags.dtype != torch.uint8 or tuple(flags.shape) != tuple(wire.shape) or flags.device != wire.device:
+            raise ValueError("flags must be a uint8 tensor of the wire's shape and device")
+        flags = flags.contiguous()
+    nbytes = lbm_porosity_workspace_size(nx, ny, nz)
+    if nbytes == 0:
+        raise LBMError(LBM_EINVAL, "bad porosity box")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=wire.device)
+    phi = torch.empty(wire.shape, dtype=torch.float32, device=wire.device)
+    s = stream if stream is not None else torch.cuda.current_stream(wire.device)
+    lbm_porosity_average(nx, ny, nz, wire.data_ptr(), flags.data_ptr() if flags is not None else 0, window,
+                         phi_min, phi.data_ptr(), ws.data_ptr(), nbytes, s.cuda_stream)
+    return phi
+
+
 # ----------------------------------------------------------------- convenience owner
 
 class Simulation:
@@ -253,7 +296,8 @@ class Simulation:
     ``problem`` is a lbm_inputs.Problem (or anything with dims, q, periodic,
     flags, phi, rheology, porous, bc).  Inputs are passed from host memory
     unless ``inputs_on_device`` is set, in which case they are copied to the
-    device first through torch.
+    device first through torch.  ``problem.phi`` may itself be a float32 CUDA
+    tensor (e.g. from :func:`porosity_average`): it is then passed as is.
     """
 
     def __init__(self, problem, storage="f32", device="cuda", stream=None, inputs_on_device=False):
@@ -265,7 +309,14 @@ class Simulation:
         self.grid = make_grid(problem.dims, problem.q, storage, problem.periodic)
         self.rheo, self.por, self.bc = make_params(problem.rheology, problem.porous, problem.bc)
         flags = np.ascontiguousarray(problem.flags, dtype=np.uint8)
-        phi = np.ascontiguousarray(problem.phi, dtype=np.float32)
+        phi_dev = problem.phi if isinstance(problem.phi, torch.Tensor) else None
+        if phi_dev is not None:
+            if phi_dev.dtype != torch.float32 or not phi_dev.is_cuda or phi_dev.numel() != flags.size:
+                raise ValueError("a device porosity must be a float32 CUDA tensor, one value per cell")
+            inputs_on_device = True
+            phi = None
+        else:
+            phi = np.ascontiguousarray(problem.phi, dtype=np.float32)
         n_list = lbm_list_length(self.grid, flags.ctypes.data)
         nbytes = lbm_workspace_size(self.grid, n_list)
         if nbytes == 0:
@@ -274,7 +325,8 @@ class Simulation:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         if inputs_on_device:
             dflags = torch.from_numpy(flags).to(self.device)
-            dphi = torch.from_numpy(phi).to(self.device)
+            dphi = (phi_dev.to(self.device).contiguous() if phi_dev is not None
+                    else torch.from_numpy(phi).to(self.device))
             fp, pp = dflags.data_ptr(), dphi.data_ptr()
         else:
             fp, pp = flags.ctypes.data, phi.ctypes.data

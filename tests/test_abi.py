@@ -96,3 +96,32 @@ def test_null_context_calls_are_safe():
     assert L.lbm_time(None) == -1
     assert L.lbm_state_size(None) == 0
     L.lbm_destroy(None)
+
+
+def test_porosity_average_host_checks():
+    """Workspace size and the argument checks of lbm_porosity_average, all of
+    which return before any device work."""
+    from paper_2402_10809_gb300 import lbm
+
+    L = lbm.load()
+    assert lbm.lbm_porosity_workspace_size(10, 4, 3) == 256 + 256
+    assert lbm.lbm_porosity_workspace_size(100, 100, 100) == 1000192 + 2000128
+    assert lbm.lbm_porosity_workspace_size(0, 4, 3) == 0
+    assert lbm.lbm_porosity_workspace_size(16385, 1, 1) == 0
+    ws = lbm.lbm_porosity_workspace_size(8, 8, 8)
+
+    def call(window=3, phi_min=0.05, wire=256, phi=256, work=256, nbytes=ws, dims=(8, 8, 8)):
+        return L.lbm_porosity_average(*dims, C.c_void_p(wire), None, window, C.c_float(phi_min),
+                                      C.c_void_p(phi), C.c_void_p(work), nbytes, None)
+
+    assert call(window=0) == lbm.LBM_EINVAL
+    assert call(window=256) == lbm.LBM_EINVAL
+    assert call(phi_min=-0.1) == lbm.LBM_EINVAL
+    assert call(phi_min=float("nan")) == lbm.LBM_EINVAL
+    assert call(phi_min=1.5) == lbm.LBM_EINVAL
+    assert call(wire=0) == lbm.LBM_EINVAL
+    assert call(phi=0) == lbm.LBM_EINVAL
+    assert call(work=0) == lbm.LBM_EINVAL
+    assert call(work=257) == lbm.LBM_EINVAL
+    assert call(nbytes=ws - 1) == lbm.LBM_ENOMEM
+    assert call(dims=(0, 8, 8)) == lbm.LBM_EINVAL
