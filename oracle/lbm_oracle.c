@@ -67,6 +67,8 @@ typedef struct {
     double* fnew;    /* [nf][q] streaming target */
     double* omega;   /* [nf] omega(t-1) */
     double* omega_new;
+    double* aniso_s;      /* [n_box][6] shape tensor S (xx yy zz xy xz yz), or NULL */
+    double* aniso_s_half; /* [n_box][6] its square root S^{1/2} */
     int64_t t;
 } oracle_ctx;
 
@@ -145,6 +147,88 @@ static void porous_closure(const oracle_ctx* o, double phi, double* inv_k, doubl
     *cf = o->p.forchheimer ? 1.75 / sqrt(150.0 * phi * phi * phi) : 0.0;
 }
 
+/* Solves X x = b for a 3x3 matrix by Gaussian elimination with partial
+ * pivoting. */
+static void solve3(const double Xin[3][3], const double b[3], double x[3])
+{
+    double X[3][4];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) X[r][c] = Xin[r][c];
+        X[r][3] = b[r];
+    }
+    for (int c = 0; c < 3; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 3; ++r)
+            if (fabs(X[r][c]) > fabs(X[piv][c])) piv = r;
+        if (piv != c)
+            for (int k = 0; k < 4; ++k) { double t = X[c][k]; X[c][k] = X[piv][k]; X[piv][k] = t; }
+        for (int r = c + 1; r < 3; ++r) {
+            double m = X[r][c] / X[c][c];
+            for (int k = c; k < 4; ++k) X[r][k] -= m * X[c][k];
+        }
+    }
+    for (int r = 2; r >= 0; --r) {
+        double acc = X[r][3];
+        for (int k = r + 1; k < 3; ++k) acc -= X[r][k] * x[k];
+        x[r] = acc / X[r][r];
+    }
+}
+
+/* Symmetric 3x3 matrix from its six components xx yy zz xy xz yz. */
+static void sym3(const double* s, double M[3][3])
+{
+    M[0][0] = s[0]; M[1][1] = s[1]; M[2][2] = s[2];
+    M[0][1] = M[1][0] = s[3];
+    M[0][2] = M[2][0] = s[4];
+    M[1][2] = M[2][1] = s[5];
+}
+
+/* Anisotropic permeability (Sec. 3, remark on the velocity solution): the drag
+ * f(u) = -phi^2 nu K^{-1} u - phi^3 C_F |u| K^{-1/2} u makes the velocity
+ * equation (A + |u| B) u = v, A = Id + (phi nu dt / 2) K^{-1},
+ * B = (phi^2 C_F dt / 2) K^{-1/2}, which the paper solves by the fixed-point
+ * iteration u_{m+1} = X_m^{-1} v, X_m = A + |u_m| B.
+ * READING: K = k(phi) S^{-1} with the isotropic closure k(phi) of
+ * porous_closure and a dimensionless SPD shape tensor S per cell, so that
+ * K^{-1} = S / k and K^{-1/2} = S^{1/2} / sqrt(k); C_F stays Ergun's scalar.
+ * READING: u_0 = v (no extra state); the iteration runs until
+ * |u_{m+1} - u_m| <= 1e-15 |v|, at most 200 times.  Returns F = rho (g + f(u)). */
+static void anisotropic_velocity(const oracle_ctx* o, int64_t idx, double phi, double rho, const double v[3],
+                                 double u[3], double F[3])
+{
+    double inv_k, inv_sqrt_k, cf;
+    porous_closure(o, phi, &inv_k, &inv_sqrt_k, &cf);
+    double S[3][3], Sh[3][3], Kinv[3][3], Kinvh[3][3], A[3][3], B[3][3];
+    sym3(o->aniso_s + idx * 6, S);
+    sym3(o->aniso_s_half + idx * 6, Sh);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            Kinv[a][b] = S[a][b] * inv_k;
+            Kinvh[a][b] = Sh[a][b] * inv_sqrt_k;
+            A[a][b] = (a == b ? 1.0 : 0.0) + phi * o->nu_d / 2.0 * Kinv[a][b];
+            B[a][b] = phi * phi * cf / 2.0 * Kinvh[a][b];
+        }
+    double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int a = 0; a < 3; ++a) u[a] = v[a];
+    for (int m = 0; m < 200; ++m) {
+        double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        double X[3][3], un1[3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) X[a][b] = A[a][b] + un * B[a][b];
+        solve3(X, v, un1);
+        double d = 0.0;
+        for (int a = 0; a < 3; ++a) { d += (un1[a] - u[a]) * (un1[a] - u[a]); u[a] = un1[a]; }
+        if (sqrt(d) <= 1e-15 * vn) break;
+    }
+    double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (int a = 0; a < 3; ++a) {
+        double fd = 0.0;
+        for (int b = 0; b < 3; ++b)
+            fd -= phi * phi * o->nu_d * Kinv[a][b] * u[b] + phi * phi * phi * cf * un * Kinvh[a][b] * u[b];
+        F[a] = rho * (o->p.g[a] + fd);
+    }
+}
+
 /* Macroscopic quantities (Sec. 3):
  *   rho = phi^{-1} sum_i f_i,
  *   u   = (phi rho)^{-1} (sum_i f_i c_i + rho f(u) / 2),
@@ -154,9 +238,10 @@ static void porous_closure(const oracle_ctx* o, double phi, double* inv_k, doubl
  * READING: a body force g (per unit mass) adds to the drag, f = g + f_d(u);
  * solving the same quadratic with v = (sum f c + rho g / 2) / (phi rho).
  * Returns F = rho (g + f_d(u)), f_d = -phi^2 nu u / k - phi^3 C_F |u| u / sqrt(k). */
-static void macroscopic(const oracle_ctx* o, const double* f, double phi, double* rho_out,
+static void macroscopic(const oracle_ctx* o, const double* f, int64_t idx, double* rho_out,
                         double u[3], double F[3])
 {
+    double phi = o->phi[idx];
     double s = 0.0, m[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < o->q; ++i) {
         s += f[i];
@@ -169,6 +254,13 @@ static void macroscopic(const oracle_ctx* o, const double* f, double phi, double
         vn += v[a] * v[a];
     }
     vn = sqrt(vn);
+    if (o->aniso_s && phi < 1.0) {
+        /* READING: the tensor acts where there is solid (phi < 1), like the
+         * constant permeability; pure fluid has no drag. */
+        anisotropic_velocity(o, idx, phi, rho, v, u, F);
+        *rho_out = rho;
+        return;
+    }
     double inv_k, inv_sqrt_k, cf;
     porous_closure(o, phi, &inv_k, &inv_sqrt_k, &cf);
     double c0 = 0.5 + phi * o->nu_d * inv_k / 4.0;
@@ -249,7 +341,7 @@ static void collide(const oracle_ctx* o, int64_t k, const double* f, double omeg
     coords(o, idx, &x, &y, &z);
     double phi = o->phi[idx];
     double rho, u[3], F[3];
-    macroscopic(o, f, phi, &rho, u, F);
+    macroscopic(o, f, idx, &rho, u, F);
     double gdot = shear_rate(o, f, phi, rho, u, F, omega_prev);
     double mu = carreau_yasuda(o, gdot);
     double om = omega_of(rho, mu);
@@ -362,7 +454,7 @@ static void extrapolation_outlet(const oracle_ctx* o, int64_t k)
     int64_t kn = o->slot[nbi];
     const double* fn = o->fnew + kn * o->q;
     double rho_nb, u_nb[3], F_nb[3];
-    macroscopic(o, fn, o->phi[nbi], &rho_nb, u_nb, F_nb);
+    macroscopic(o, fn, nbi, &rho_nb, u_nb, F_nb);
     for (int i = 0; i < o->q; ++i)
         if (o->c[i][ax] * sgn > 0)
             f[i] = equilibrium(o, i, o->phi[idx], o->p.rho_out, u_nb) + fn[i] - equilibrium(o, i, o->phi[nbi], rho_nb, u_nb);
@@ -485,7 +577,28 @@ void oracle_destroy(oracle_ctx* o)
     if (!o) return;
     free(o->flags); free(o->phi); free(o->slot); free(o->cell);
     free(o->f); free(o->fpost); free(o->fnew); free(o->omega); free(o->omega_new);
+    free(o->aniso_s); free(o->aniso_s_half);
     free(o);
+}
+
+/* Anisotropic permeability from now on (see anisotropic_velocity): the shape
+ * tensor S and its square root per box cell, [n_box][6] (xx yy zz xy xz yz);
+ * NULL returns to the isotropic closure.  Returns 0, or 2 when out of memory. */
+int32_t oracle_set_anisotropy(oracle_ctx* o, const double* s, const double* s_half)
+{
+    free(o->aniso_s); free(o->aniso_s_half);
+    o->aniso_s = o->aniso_s_half = NULL;
+    if (!s) return 0;
+    o->aniso_s = (double*)malloc(o->n_box * 6 * sizeof(double));
+    o->aniso_s_half = (double*)malloc(o->n_box * 6 * sizeof(double));
+    if (!o->aniso_s || !o->aniso_s_half) {
+        free(o->aniso_s); free(o->aniso_s_half);
+        o->aniso_s = o->aniso_s_half = NULL;
+        return 2;
+    }
+    memcpy(o->aniso_s, s, o->n_box * 6 * sizeof(double));
+    memcpy(o->aniso_s_half, s_half, o->n_box * 6 * sizeof(double));
+    return 0;
 }
 
 /* n time steps: collide every fluid cell, push, bounce back, reconstruct the
@@ -524,7 +637,7 @@ void oracle_moments(const oracle_ctx* o, double* rho, double* ux, double* uy, do
         int64_t idx = o->cell[k];
         double phi = o->phi[idx], r, u[3], F[3];
         const double* f = o->f + k * o->q;
-        macroscopic(o, f, phi, &r, u, F);
+        macroscopic(o, f, idx, &r, u, F);
         double g = shear_rate(o, f, phi, r, u, F, o->omega[k]);
         rho[idx] = r; ux[idx] = u[0]; uy[idx] = u[1]; uz[idx] = u[2];
         gdot[idx] = g;
@@ -564,7 +677,7 @@ void oracle_wss(const oracle_ctx* o, double* wss)
         for (int a = 0; a < 3; ++a) nrm[a] /= nn;
         double phi = o->phi[idx], r, u[3], F[3];
         const double* f = o->f + k * o->q;
-        macroscopic(o, f, phi, &r, u, F);
+        macroscopic(o, f, idx, &r, u, F);
         double pi[3][3];
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) pi[a][b] = 0.5 * (F[a] * u[b] + u[a] * F[b]);
@@ -604,7 +717,7 @@ void oracle_diag(const oracle_ctx* o, const uint8_t* region, double* out)
         double s = 0.0;
         for (int i = 0; i < o->q; ++i) s += f[i];
         double phi = o->phi[idx], r, u[3], F[3];
-        macroscopic(o, f, phi, &r, u, F);
+        macroscopic(o, f, idx, &r, u, F);
         double g = shear_rate(o, f, phi, r, u, F, o->omega[k]);
         double om = omega_of(r, carreau_yasuda(o, g));
         double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
@@ -635,7 +748,7 @@ double oracle_run_objective(oracle_ctx* o, int64_t T, const uint8_t* region)
             int64_t idx = o->cell[k];
             if (!region[idx]) continue;
             double r, u[3], F[3];
-            macroscopic(o, o->f + k * o->q, o->phi[idx], &r, u, F);
+            macroscopic(o, o->f + k * o->q, idx, &r, u, F);
             ke += 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
             cnt += 1.0;
         }

@@ -79,6 +79,8 @@ def lib():
             L.oracle_apply_boundaries.argtypes = [C.c_void_p, C.c_int64]
             L.oracle_lattice_params.argtypes = [C.c_void_p, d]
             L.oracle_num_threads.restype = C.c_int32
+            L.oracle_set_anisotropy.restype = C.c_int32
+            L.oracle_set_anisotropy.argtypes = [C.c_void_p, d, d]
             _lib = L
     return _lib
 
@@ -107,10 +109,33 @@ def params_from_problem(prob):
     return o
 
 
-class Oracle:
-    """FP64 reference simulation of one Problem."""
+def shape_tensor_sqrt(S):
+    """Per-cell square root of the symmetric positive definite shape tensor:
+    S is (6, ...) with components xx yy zz xy xz yz; returns the same layout.
+    Through the eigendecomposition S = V diag(l) V^T (numpy.linalg.eigh),
+    S^{1/2} = V diag(sqrt(l)) V^T."""
+    S = np.asarray(S, dtype=np.float64)
+    sh = S.shape[1:]
+    s = S.reshape(6, -1)
+    M = np.empty((s.shape[1], 3, 3))
+    for (a, b), c in (((0, 0), 0), ((1, 1), 1), ((2, 2), 2), ((0, 1), 3), ((0, 2), 4), ((1, 2), 5)):
+        M[:, a, b] = s[c]
+        M[:, b, a] = s[c]
+    lam, V = np.linalg.eigh(M)
+    if not np.all(lam > 0):
+        raise ValueError("shape tensor not positive definite")
+    H = np.einsum("nab,nb,ncb->nac", V, np.sqrt(lam), V)
+    out = np.stack([H[:, 0, 0], H[:, 1, 1], H[:, 2, 2], H[:, 0, 1], H[:, 0, 2], H[:, 1, 2]])
+    return out.reshape((6,) + sh)
 
-    def __init__(self, prob, phi=None):
+
+class Oracle:
+    """FP64 reference simulation of one Problem.  ``shape_tensor``: optional
+    (6, nz, ny, nx) symmetric positive definite tensor S per cell (xx yy zz xy
+    xz yz) for the anisotropic permeability K = k(phi) S^{-1} of the velocity
+    solve's fixed-point iteration (Sec. 3 remark)."""
+
+    def __init__(self, prob, phi=None, shape_tensor=None):
         self.L = lib()
         self.prob = prob
         self.params = params_from_problem(prob)
@@ -129,6 +154,14 @@ class Oracle:
         self.q = self.L.oracle_q(self.h)
         self.nf = self.L.oracle_nfluid(self.h)
         self.shape = self.flags.shape
+        if shape_tensor is not None:
+            S = np.asarray(shape_tensor, dtype=np.float64)
+            if S.shape != (6,) + self.shape:
+                raise ValueError("shape_tensor must be (6, nz, ny, nx)")
+            s = np.ascontiguousarray(S.reshape(6, -1).T)
+            h = np.ascontiguousarray(shape_tensor_sqrt(S).reshape(6, -1).T)
+            if self.L.oracle_set_anisotropy(self.h, _dptr(s), _dptr(h)) != 0:
+                raise MemoryError("oracle_set_anisotropy")
 
     def close(self):
         if self.h:
