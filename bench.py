@@ -147,8 +147,10 @@ def flush_l2(torch, buf):
     buf.fill_(1.0)
 
 
-def time_variant(torch, lbm, prob, storage, steps, warmup, lbm_steps, flush):
+def time_variant(torch, lbm, prob, storage, steps, warmup, lbm_steps, flush, setup=None):
     sim = lbm.Simulation(prob, storage=storage)
+    if setup is not None:
+        setup(sim)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         flush_l2(torch, flush)
@@ -288,6 +290,8 @@ def run_ours(args):
     }
     if rank == 0:
         line["wall_shear"] = wall_shear_pass(torch, lbm, sim, prob, stream)
+    if rank == 0 and not args.no_aniso:
+        line["anisotropic"] = aniso_cost(torch, lbm, prob, args, flush, mlups / ws)
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = adjoint_cost(torch, lbm, args)
     if rank == 0 and not args.no_coil:
@@ -368,6 +372,40 @@ def adjoint_cost(torch, lbm, args):
         del ws
     sim.close()
     return res
+
+
+def aniso_cost(torch, lbm, prob, args, flush, iso_value):
+    """Cost of the anisotropic velocity solve (Sec. 3 remark: fixed-point
+    iteration with a 3x3 solve per step) against the explicit solve of the
+    headline, on the same workload and protocol (warm-up, L2 flush, CUDA
+    events): the porous sac gets a seeded coil shape tensor (wire direction
+    field, 4 times more permeable along the wire; lbm_inputs.coil_shape_tensor),
+    the rest of the box S = Id.  Algorithmic bytes per porous cell update rise
+    by 48 (A - Id and B, 12 floats)."""
+    from lbm_inputs import coil_shape_tensor
+
+    por = (prob.phi < 1) & (prob.flags > 0)
+    idx = np.nonzero(por)
+    lo = [int(a.min()) for a in idx]
+    hi = [int(a.max()) + 1 for a in idx]
+    S = np.zeros((6,) + prob.flags.shape, np.float32)
+    S[:3] = 1.0
+    S[:, lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]] = coil_shape_tensor(tuple(h - l for l, h in zip(lo, hi)),
+                                                                      ratio=4.0, seed=0)
+    iters, tol = 16, 1e-6
+    L = args.lbm_steps
+    sim, tv = time_variant(torch, lbm, prob, "f32", max(3, args.steps // 2), args.warmup, L, flush,
+                           setup=lambda s: s.set_anisotropy(S, max_iter=iters, tol=tol))
+    finite = bool(sim.diag()[7] == 0)
+    sim.close()
+    nf, npor = prob.n_fluid, int(por.sum())
+    t = sum(tv) / len(tv)
+    value = nf * L / t / 1e6
+    bpu = bytes_per_update(WORKLOAD["q"], "f32") + 48.0 * npor / nf
+    peak, _ = load_peaks()
+    return {"value": value, "unit": UNIT, "vs_explicit": value / iso_value, "porous_cells": npor,
+            "max_iter": iters, "tol": tol, "bytes_per_update": bpu,
+            "roofline_frac": bpu * nf * L / t / 1e9 / peak, "finite": finite}
 
 
 def wall_shear_pass(torch, lbm, sim, prob, stream):
@@ -595,6 +633,7 @@ def main():
     ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="aneurysm box edge")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16dev", "bf16dev"])
     ap.add_argument("--no-coil", action="store_true", help="skip the resolved / averaged coil study")
+    ap.add_argument("--no-aniso", action="store_true", help="skip the anisotropic-permeability cost")
     ap.add_argument("--coil-n", type=int, default=512)
     ap.add_argument("--coil-steps", type=int, default=5000)
     ap.add_argument("--adjoint-n", type=int, default=ADJOINT["n"])

@@ -181,6 +181,36 @@ lbm_status lbm_wall_shear(lbm_ctx* ctx, float* wss, int32_t dst_on_device);
  *    them.  No state carries over from one call to the next. */
 lbm_status lbm_diag_noalloc(lbm_ctx* ctx, const uint8_t* region, double out[8]);
 
+/* Anisotropic permeability (Sec. 3 remark on the velocity solution).  The
+ * drag becomes f(u) = -phi^2 nu K^{-1} u - phi^3 C_F |u| K^{-1/2} u with
+ * K = k(phi) S^{-1}: k(phi) and C_F the isotropic closure of lbm_init
+ * (Kozeny-Carman or constant permeability, Ergun's C_F; nu the Darcy
+ * viscosity) and S a symmetric positive definite shape tensor per cell
+ * (S = Id is the isotropic medium).  Every later step, moments, diag and
+ * wall-shear call solves the velocity equation (A + |u| B) u = v,
+ * A = Id + (phi nu / 2) K^{-1}, B = (phi^2 C_F / 2) K^{-1/2}, at each cell with
+ * phi < 1 by the fixed-point iteration u_{m+1} = (A + |u_m| B)^{-1} v from
+ * u_0 = v, until |u_{m+1} - u_m| <= tol |v| or max_iter iterations (FP32);
+ * cells with phi = 1 keep the explicit solution.
+ *  - shape:  [6][nz][ny][nx] float, components xx yy zz xy xz yz (each a
+ *            dense plane); device memory; read only during the call.  NULL
+ *            switches back to the isotropic closure.
+ *  - buffer / bytes: caller-owned device memory (256-byte aligned) of at least
+ *            lbm_anisotropy_buffer_size(ctx) bytes (12 floats per slot of the
+ *            packed layout) that the context keeps using until the next
+ *            lbm_set_anisotropy or lbm_destroy.  The set-up stores A - Id and
+ *            B per slot there, with S^{1/2} from an FP64 Jacobi
+ *            eigendecomposition.
+ *  - max_iter 1..1000, 0 <= tol < 1 (1e-6 and 16 converge to FP32 round-off
+ *            for blood-flow drag).
+ * FP32 storage only (LBM_EINVAL otherwise).  LBM_EINVAL when S is not finite
+ * or not positive definite at a cell with phi < 1; LBM_ENOMEM when the buffer
+ * is too small.  lbm_adjoint returns LBM_ESTATE while the tensor is set (its
+ * reverse covers the explicit velocity solve only).  Synchronises the stream. */
+size_t lbm_anisotropy_buffer_size(const lbm_ctx* ctx);
+lbm_status lbm_set_anisotropy(lbm_ctx* ctx, const float* shape, void* buffer, size_t bytes, int32_t max_iter,
+                              float tol);
+
 /* Volume-averaged porosity of a voxelised coil, the input that lbm_init takes
  * as the porosity of the averaged simulations (Sec. 4: the porosity field is
  * the windowed convolution of the voxelised coil with a uniform averaging

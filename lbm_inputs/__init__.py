@@ -18,7 +18,14 @@ from .geometry import (  # noqa: F401
     channel_flags,
     periodic_box_flags,
 )
-from .porosity import coil_packings, plug_porosity, sac_random_porosity, wire_coil, wire_coil_order  # noqa: F401
+from .porosity import (  # noqa: F401
+    coil_packings,
+    coil_shape_tensor,
+    plug_porosity,
+    sac_random_porosity,
+    wire_coil,
+    wire_coil_order,
+)
 from .configs import (  # noqa: F401
     Problem,
     pipe_problem,

@@ -108,3 +108,23 @@ def wire_coil_order(n, packing=0.25, seed=0, thickness_radius=1, small=False):
                 wire[z, y, x] = count
                 count += 1
     return wire
+
+
+def coil_shape_tensor(shape, ratio=4.0, sigma=3.0, seed=0):
+    """Seeded shape tensor S of an anisotropic coil medium, (6, nz, ny, nx)
+    float32, components xx yy zz xy xz yz: S = t t^T / ratio + (Id - t t^T)
+    with t(x) a smooth random unit vector (i.i.d. normal vector components
+    filtered with a Gaussian of ``sigma`` voxels, then normalised), the local
+    wire direction.  Eigenvalues 1/ratio along t and 1 across it: the medium
+    is ``ratio`` times more permeable along the wire than across it."""
+    from scipy.ndimage import gaussian_filter
+
+    rng = np.random.default_rng(seed)
+    t = np.stack([gaussian_filter(rng.standard_normal(shape, dtype=np.float32), sigma=sigma, mode="wrap")
+                  for _ in range(3)])
+    t /= np.maximum(np.sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]), np.float32(1e-12))
+    a = np.float32(1.0 / ratio - 1.0)
+    S = np.empty((6,) + tuple(shape), dtype=np.float32)
+    for k, (i, j) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))):
+        S[k] = a * t[i] * t[j] + np.float32(1.0 if i == j else 0.0)
+    return S

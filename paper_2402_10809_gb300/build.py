@@ -19,7 +19,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v
 
 EXTRA = os.environ.get("LBM_NVCC_EXTRA", "").split()
 UNITS = [("setup", "setup.cu", []), ("api", "api.cu", []), ("wss", "wss.cu", ["--use_fast_math"]),
-         ("porosity", "porosity.cu", [])]
+         ("porosity", "porosity.cu", []), ("aniso", "aniso.cu", [])]
 for q in (19, 27):
     for s, name in ((0, "f32"), (1, "f16"), (2, "bf16")):
         UNITS.append((f"step_{q}_{name}", "step.cu", [f"-DLBM_Q={q}", f"-DLBM_STORE={s}", "--use_fast_math"]))

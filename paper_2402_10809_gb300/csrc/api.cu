@@ -24,6 +24,7 @@ cudaError_t launch_step_27_f32(int, const Params&, cudaStream_t);
 cudaError_t launch_step_27_f16(int, const Params&, cudaStream_t);
 cudaError_t launch_step_27_bf16(int, const Params&, cudaStream_t);
 cudaError_t launch_wall_shear(int q, int storage, const Params& P, float* out, int compact, cudaStream_t s);
+cudaError_t launch_setup_aniso(const Params& P, const float* S, long long N, float* out, uint32_t* err, cudaStream_t s);
 cudaError_t launch_adjoint_19_f32(int, const AdjParams&, cudaStream_t);
 cudaError_t launch_adjoint_19_f16(int, const AdjParams&, cudaStream_t);
 cudaError_t launch_adjoint_19_bf16(int, const AdjParams&, cudaStream_t);
@@ -575,6 +576,45 @@ extern "C" lbm_status lbm_wall_shear(lbm_ctx* c, float* wss, int32_t dst_on_devi
     return LBM_OK;
 }
 
+extern "C" size_t lbm_anisotropy_buffer_size(const lbm_ctx* c)
+{
+    if (!c || !c->ready) return 0;
+    return align256(12 * sizeof(float) * (size_t)c->n_store);
+}
+
+extern "C" lbm_status lbm_set_anisotropy(lbm_ctx* c, const float* shape, void* buffer, size_t bytes, int32_t max_iter,
+                                         float tol)
+{
+    if (!c) return LBM_EINVAL;
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    if (!shape) {
+        c->base.aniso = nullptr;
+        return LBM_OK;
+    }
+    if (c->grid.storage != LBM_F32) return fail(c, LBM_EINVAL, "the anisotropic velocity solve needs FP32 storage");
+    if (!buffer || reinterpret_cast<uintptr_t>(buffer) % 256 != 0)
+        return fail(c, LBM_EINVAL, "anisotropy buffer null or not 256-byte aligned");
+    if (bytes < lbm_anisotropy_buffer_size(c)) return fail(c, LBM_ENOMEM, "anisotropy buffer too small");
+    if (max_iter < 1 || max_iter > 1000 || !(tol >= 0.0f && tol < 1.0f))
+        return fail(c, LBM_EINVAL, "max_iter must be 1..1000 and 0 <= tol < 1");
+    uint32_t* errw = c->at<uint32_t>(c->L.err) + 5;
+    LBM_CUDA(cudaMemsetAsync(errw, 0, 4, c->stream), "clear error word");
+    Params P = c->base;
+    LBM_CUDA(launch_setup_aniso(P, shape, (long long)c->N, static_cast<float*>(buffer), errw, c->stream),
+             "anisotropy set-up kernel");
+    uint32_t e = 0;
+    LBM_CUDA(cudaMemcpyAsync(&e, errw, 4, cudaMemcpyDeviceToHost, c->stream), "copy error word");
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "anisotropy set-up sync");
+    if (e) {
+        c->base.aniso = nullptr;
+        return fail(c, LBM_EINVAL, "shape tensor not finite or not positive definite at a cell with phi < 1");
+    }
+    c->base.aniso = static_cast<const float*>(buffer);
+    c->base.aniso_iters = max_iter;
+    c->base.aniso_tol = tol;
+    return LBM_OK;
+}
+
 static bool porosity_dims_ok(int32_t nx, int32_t ny, int32_t nz)
 {
     return nx >= 1 && ny >= 1 && nz >= 1 && nx <= kPorosityMaxNx && (long long)nx * ny * nz <= (1ll << 40);
@@ -763,6 +803,8 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, int32_t obje
     if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
     if (T < 1 || K < 1) return fail(c, LBM_EINVAL, "T and K must be >= 1");
     if (objective != 0 && objective != 1) return fail(c, LBM_EINVAL, "objective must be 0 (kinetic energy) or 1 (wall shear)");
+    if (c->base.aniso)
+        return fail(c, LBM_ESTATE, "the adjoint does not cover the anisotropic velocity solve (lbm_set_anisotropy)");
     if (!region || !workspace || !grad || !J) return fail(c, LBM_EINVAL, "null pointer argument");
     if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
         return fail(c, LBM_EINVAL, "adjoint workspace not 256-byte aligned");

@@ -86,6 +86,11 @@ struct Params {
     float *o_rho, *o_ux, *o_uy, *o_uz, *o_gdot, *o_omega;
     int o_compact;
     float* o_drho;            // time step: rho - 1 of time t per slot (may be null)
+    // anisotropic permeability (kernels instantiated with AN = true): per slot
+    // [12][n_store] Ah xx yy zz xy xz yz, then B in the same order
+    const float* aniso;
+    int aniso_iters;
+    float aniso_tol;
     // diagnostics
     const uint8_t* region;    // dense, may be null
     double* partials;         // [gridDim.x][kDiagSlots]
@@ -221,6 +226,68 @@ __device__ __forceinline__ Macro macroscopic(const Params& P, float phi, float s
     M.Fx = fmaf(M.rho, P.gx, -s2 * M.ux);
     M.Fy = fmaf(M.rho, P.gy, -s2 * M.uy);
     M.Fz = fmaf(M.rho, P.gz, -s2 * M.uz);
+    return M;
+}
+
+// Anisotropic permeability (Sec. 3 remark).  With K = k(phi) S^{-1} (the
+// isotropic closure k(phi) and a per-cell shape tensor S) the drag
+// f(u) = -phi^2 nu K^{-1} u - phi^3 C_F |u| K^{-1/2} u turns the velocity
+// equation into (Id + Ah + |u| B) u = v, Ah = (phi nu / 2) K^{-1},
+// B = (phi^2 C_F / 2) K^{-1/2}, both precomputed per slot.  Fixed-point
+// iteration u_{m+1} = (Id + Ah + |u_m| B)^{-1} v from u_0 = v, each step one
+// 3x3 solve by the adjugate, until |u_{m+1} - u_m| <= tol |v| or aniso_iters
+// steps; then F = rho g - 2 phi rho (Ah u + |u| B u).  Cells with phi = 1 have
+// no medium and take the explicit solution.
+__device__ __forceinline__ Macro macroscopic_aniso(const Params& P, int p, float phi, float sd, float mx, float my,
+                                                   float mz)
+{
+    if (!(phi < 1.0f)) return macroscopic(P, phi, sd, mx, my, mz);
+    Macro M;
+    M.sd = sd;
+    M.sigma = phi + sd;
+    const float iphi = __frcp_rn(phi);
+    M.rho = M.sigma * iphi;
+    M.drho = sd * iphi;
+    const float isig = __fdividef(1.0f, M.sigma);
+    const float hg = 0.5f * iphi;
+    const float vx = fmaf(P.gx, hg, mx * isig);
+    const float vy = fmaf(P.gy, hg, my * isig);
+    const float vz = fmaf(P.gz, hg, mz * isig);
+    const size_t n = (size_t)P.n_store;
+    const float* a = P.aniso + p;
+    const float axx = __ldg(a), ayy = __ldg(a + n), azz = __ldg(a + 2 * n);
+    const float axy = __ldg(a + 3 * n), axz = __ldg(a + 4 * n), ayz = __ldg(a + 5 * n);
+    const float bxx = __ldg(a + 6 * n), byy = __ldg(a + 7 * n), bzz = __ldg(a + 8 * n);
+    const float bxy = __ldg(a + 9 * n), bxz = __ldg(a + 10 * n), byz = __ldg(a + 11 * n);
+    const float tol = P.aniso_tol * sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
+    float ux = vx, uy = vy, uz = vz, un = sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+    for (int m = 0; m < P.aniso_iters; ++m) {
+        const float xx = 1.0f + fmaf(un, bxx, axx), yy = 1.0f + fmaf(un, byy, ayy), zz = 1.0f + fmaf(un, bzz, azz);
+        const float xy = fmaf(un, bxy, axy), xz = fmaf(un, bxz, axz), yz = fmaf(un, byz, ayz);
+        const float c00 = fmaf(yy, zz, -yz * yz), c01 = fmaf(xz, yz, -xy * zz), c02 = fmaf(xy, yz, -yy * xz);
+        const float c11 = fmaf(xx, zz, -xz * xz), c12 = fmaf(xy, xz, -xx * yz), c22 = fmaf(xx, yy, -xy * xy);
+        const float idet = __frcp_rn(fmaf(xx, c00, fmaf(xy, c01, xz * c02)));
+        const float nx = fmaf(c00, vx, fmaf(c01, vy, c02 * vz)) * idet;
+        const float ny = fmaf(c01, vx, fmaf(c11, vy, c12 * vz)) * idet;
+        const float nz = fmaf(c02, vx, fmaf(c12, vy, c22 * vz)) * idet;
+        const float dx = nx - ux, dy = ny - uy, dz = nz - uz;
+        ux = nx;
+        uy = ny;
+        uz = nz;
+        un = sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+        if (sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) <= tol) break;
+    }
+    M.ux = ux;
+    M.uy = uy;
+    M.uz = uz;
+    // drag per unit phi rho, halved: Ah u + |u| B u
+    const float dxv = fmaf(axx, ux, fmaf(axy, uy, axz * uz)) + un * fmaf(bxx, ux, fmaf(bxy, uy, bxz * uz));
+    const float dyv = fmaf(axy, ux, fmaf(ayy, uy, ayz * uz)) + un * fmaf(bxy, ux, fmaf(byy, uy, byz * uz));
+    const float dzv = fmaf(axz, ux, fmaf(ayz, uy, azz * uz)) + un * fmaf(bxz, ux, fmaf(byz, uy, bzz * uz));
+    const float s2 = 2.0f * M.sigma;
+    M.Fx = fmaf(M.rho, P.gx, -s2 * dxv);
+    M.Fy = fmaf(M.rho, P.gy, -s2 * dyv);
+    M.Fz = fmaf(M.rho, P.gz, -s2 * dzv);
     return M;
 }
 
@@ -514,7 +581,7 @@ __device__ __forceinline__ void block_reduce_diag(double* v, double* partials)
 // collision, store).  kModeMoments: pull + boundaries + moments and fields of
 // the current time.  kModeDiag: the same fields reduced to diagnostics.
 // park: this thread's column of a Q x kBlock shared array (time step only).
-template <int Q, class T, int MODE, bool fast>
+template <int Q, class T, int MODE, bool fast, bool AN>
 __device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t mask, double* dv, volatile float* park)
 {
     using L = Lattice<Q>;
@@ -557,7 +624,11 @@ __device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t mask,
         for (int i = 0; i < Q; ++i) park[i * kBlock] = g[i];
     }
     const Moments<Q> m = moments<Q>(g);
-    const Macro M = macroscopic(P, phi, m.sd, m.mx, m.my, m.mz);
+    Macro M;
+    if constexpr (AN)
+        M = macroscopic_aniso(P, p, phi, m.sd, m.mx, m.my, m.mz);
+    else
+        M = macroscopic(P, phi, m.sd, m.mx, m.my, m.mz);
     // corrected second moment Pi (Sec. 3), via sum f^eq c c = phi rho (c_s^2 I + u u)
     const float sd3 = M.sd * (1.0f / 3.0f);
     const float pxx = fmaf(M.ux, fmaf(-M.sigma, M.ux, M.Fx), m.sxx - sd3);
@@ -657,10 +728,10 @@ __device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t mask,
 
 // Cells of the general path (periodic wrap, inlet, outlet) in a function of
 // their own, so that their register needs do not bound the lean path.
-template <int Q, class T, int MODE>
+template <int Q, class T, int MODE, bool AN>
 __device__ __noinline__ void cell_general(const Params& P, int p, uint32_t mask, double* dv, volatile float* park)
 {
-    cell_impl<Q, T, MODE, false>(P, p, mask, dv, park);
+    cell_impl<Q, T, MODE, false, AN>(P, p, mask, dv, park);
 }
 
 // A ghost slot: complete its sectors with zeros where it shares an aligned
@@ -677,13 +748,13 @@ __device__ __forceinline__ void ghost_slot(const Params& P, int p, uint32_t mask
 
 // Lean-path thread of slot p: ghost slots store zeros where needed, general
 // cells are left to the general blocks.
-template <int Q, class T, int MODE>
+template <int Q, class T, int MODE, bool AN>
 __device__ __forceinline__ void lean_body(const Params& P, int p, uint32_t mask, double* dv, volatile float* park)
 {
     if (mask & kGhostBit)
         ghost_slot<Q, T, MODE>(P, p, mask);
     else if (!(mask & kGeneralBits) && !P.wide)
-        cell_impl<Q, T, MODE, true>(P, p, mask, dv, park);
+        cell_impl<Q, T, MODE, true, AN>(P, p, mask, dv, park);
 }
 
 // Shared column for parking the pulled populations during a time step.
@@ -697,8 +768,9 @@ __device__ __forceinline__ volatile float* park_column()
 
 // MODE kModeStep: full time step (pull, boundaries, moments, relaxation rate,
 // collision, store).  kModeMoments: pull + boundaries + moments and fields of
-// the current time.  kModeDiag: the same fields reduced to diagnostics.
-template <int Q, class T, int MODE>
+// the current time.  kModeDiag: the same fields reduced to diagnostics.  AN:
+// the anisotropic velocity solve (macroscopic_aniso) at porous cells.
+template <int Q, class T, int MODE, bool AN = false>
 __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS) lbm_kernel(const Params P)
 {
     const int nbg = general_blocks(P);
@@ -710,11 +782,11 @@ __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS) lbm_kernel(const Param
         const int k = (int)blockIdx.x * P.gen_block + (int)threadIdx.x;
         if ((int)threadIdx.x < P.gen_block && k < P.n_general) {
             const int p = (int)P.general[k];
-            cell_general<Q, T, MODE>(P, p, P.mask[p], dv, park);
+            cell_general<Q, T, MODE, AN>(P, p, P.mask[p], dv, park);
         }
     } else {
         const int p = ((int)blockIdx.x - nbg) * kBlock + (int)threadIdx.x;
-        if (p < P.n_store) lean_body<Q, T, MODE>(P, p, P.mask[p], dv, park);
+        if (p < P.n_store) lean_body<Q, T, MODE, AN>(P, p, P.mask[p], dv, park);
     }
     if (MODE == kModeDiag) block_reduce_diag(dv, P.partials);
 }

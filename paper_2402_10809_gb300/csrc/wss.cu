@@ -17,7 +17,7 @@
 
 namespace lbm {
 
-template <int Q, class T>
+template <int Q, class T, bool AN>
 __global__ void __launch_bounds__(kBlock) wall_shear_kernel(const Params P, float* __restrict__ out, int compact)
 {
     using L = Lattice<Q>;
@@ -43,7 +43,11 @@ __global__ void __launch_bounds__(kBlock) wall_shear_kernel(const Params P, floa
     float g[Q];
     pull_general<Q, T>(P, static_cast<const T*>(P.fsrc), c, mask, g);
     const Moments<Q> m = moments<Q>(g);
-    const Macro M = macroscopic(P, __ldg(P.phi + p), m.sd, m.mx, m.my, m.mz);
+    Macro M;
+    if constexpr (AN)
+        M = macroscopic_aniso(P, p, __ldg(P.phi + p), m.sd, m.mx, m.my, m.mz);
+    else
+        M = macroscopic(P, __ldg(P.phi + p), m.sd, m.mx, m.my, m.mz);
     // corrected second moment Pi (as for the shear rate of the step)
     const float sd3 = M.sd * (1.0f / 3.0f);
     const float pxx = fmaf(M.ux, fmaf(-M.sigma, M.ux, M.Fx), m.sxx - sd3);
@@ -69,14 +73,17 @@ cudaError_t launch_wall_shear(int q, int storage, const Params& P, float* out, i
 {
     const int grid = (P.n_store + kBlock - 1) / kBlock;
     if (grid == 0) return cudaSuccess;
+    if (P.aniso && storage != 0) return cudaErrorInvalidValue;  // anisotropic solve: FP32 storage only
     if (q == 19) {
-        if (storage == 0) wall_shear_kernel<19, float><<<grid, kBlock, 0, s>>>(P, out, compact);
-        else if (storage == 1) wall_shear_kernel<19, __half><<<grid, kBlock, 0, s>>>(P, out, compact);
-        else wall_shear_kernel<19, __nv_bfloat16><<<grid, kBlock, 0, s>>>(P, out, compact);
+        if (P.aniso) wall_shear_kernel<19, float, true><<<grid, kBlock, 0, s>>>(P, out, compact);
+        else if (storage == 0) wall_shear_kernel<19, float, false><<<grid, kBlock, 0, s>>>(P, out, compact);
+        else if (storage == 1) wall_shear_kernel<19, __half, false><<<grid, kBlock, 0, s>>>(P, out, compact);
+        else wall_shear_kernel<19, __nv_bfloat16, false><<<grid, kBlock, 0, s>>>(P, out, compact);
     } else {
-        if (storage == 0) wall_shear_kernel<27, float><<<grid, kBlock, 0, s>>>(P, out, compact);
-        else if (storage == 1) wall_shear_kernel<27, __half><<<grid, kBlock, 0, s>>>(P, out, compact);
-        else wall_shear_kernel<27, __nv_bfloat16><<<grid, kBlock, 0, s>>>(P, out, compact);
+        if (P.aniso) wall_shear_kernel<27, float, true><<<grid, kBlock, 0, s>>>(P, out, compact);
+        else if (storage == 0) wall_shear_kernel<27, float, false><<<grid, kBlock, 0, s>>>(P, out, compact);
+        else if (storage == 1) wall_shear_kernel<27, __half, false><<<grid, kBlock, 0, s>>>(P, out, compact);
+        else wall_shear_kernel<27, __nv_bfloat16, false><<<grid, kBlock, 0, s>>>(P, out, compact);
     }
     return cudaGetLastError();
 }

@@ -23,7 +23,8 @@ SYMBOLS = ["lbm_list_length", "lbm_workspace_size", "lbm_init", "lbm_step", "lbm
            "lbm_set_check",
            "lbm_state_size", "lbm_save", "lbm_load", "lbm_time", "lbm_fluid_count", "lbm_last_error",
            "lbm_destroy", "lbm_adjoint_workspace_size", "lbm_adjoint", "lbm_wall_shear",
-           "lbm_porosity_workspace_size", "lbm_porosity_average"]
+           "lbm_porosity_workspace_size", "lbm_porosity_average", "lbm_anisotropy_buffer_size",
+           "lbm_set_anisotropy"]
 
 
 class lbm_grid(C.Structure):
@@ -108,6 +109,10 @@ def load(build_if_missing=True):
     L.lbm_adjoint_workspace_size.argtypes = [vp, C.c_int32, C.c_int32]
     L.lbm_adjoint.restype = C.c_int
     L.lbm_adjoint.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, vp, C.c_int32, vp, C.c_size_t, vp, P(C.c_double)]
+    L.lbm_anisotropy_buffer_size.restype = C.c_size_t
+    L.lbm_anisotropy_buffer_size.argtypes = [vp]
+    L.lbm_set_anisotropy.restype = C.c_int
+    L.lbm_set_anisotropy.argtypes = [vp, vp, vp, C.c_size_t, C.c_int32, C.c_float]
     L.lbm_porosity_workspace_size.restype = C.c_size_t
     L.lbm_porosity_workspace_size.argtypes = [C.c_int32, C.c_int32, C.c_int32]
     L.lbm_porosity_average.restype = C.c_int
@@ -251,6 +256,16 @@ def lbm_adjoint(ctx, T, K, objective, region, region_on_device, workspace, works
     return float(J.value)
 
 
+def lbm_anisotropy_buffer_size(ctx):
+    return int(load().lbm_anisotropy_buffer_size(ctx))
+
+
+def lbm_set_anisotropy(ctx, shape, buffer, buffer_bytes, max_iter, tol):
+    """shape / buffer: device addresses (shape 0 returns to the isotropic closure)."""
+    _check(ctx, load().lbm_set_anisotropy(ctx, C.c_void_p(shape or None), C.c_void_p(buffer or None),
+                                          C.c_size_t(buffer_bytes), int(max_iter), C.c_float(tol)))
+
+
 def lbm_porosity_workspace_size(nx, ny, nz):
     return int(load().lbm_porosity_workspace_size(int(nx), int(ny), int(nz)))
 
@@ -373,6 +388,24 @@ class Simulation:
         om = np.zeros(self.shape, np.float32)
         lbm_moments(self.ctx, rho.ctypes.data, u.ctypes.data, g.ctypes.data, om.ctypes.data, 0)
         return dict(rho=rho, u=u, gdot=g, omega=om)
+
+    def set_anisotropy(self, shape, max_iter=16, tol=1e-6):
+        """Anisotropic permeability K = k(phi) S^{-1}: ``shape`` is the
+        (6, nz, ny, nx) shape tensor S (xx yy zz xy xz yz; numpy or a CUDA
+        tensor), or None for the isotropic closure."""
+        torch = self.torch
+        if shape is None:
+            lbm_set_anisotropy(self.ctx, 0, 0, 0, max_iter, tol)
+            self._aniso = None
+            return
+        S = shape if isinstance(shape, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(shape, np.float32))
+        S = S.to(device=self.device, dtype=torch.float32).contiguous()
+        if tuple(S.shape) != (6,) + tuple(self.shape):
+            raise ValueError("shape tensor must be (6, nz, ny, nx)")
+        nbytes = lbm_anisotropy_buffer_size(self.ctx)
+        buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        lbm_set_anisotropy(self.ctx, S.data_ptr(), buf.data_ptr(), nbytes, max_iter, tol)
+        self._aniso = buf  # the context keeps using it
 
     def wall_shear(self, on_device=False):
         """Voxel wall-shear-stress proxy |tau| of the current time on the dense box."""
