@@ -171,7 +171,7 @@ lbm_status lbm_wall_shear(lbm_ctx* ctx, float* wss, int32_t dst_on_device);
  *  - Limit: at most 8,388,608 slots of the packed layout (lbm_list_length)
  *    and 1,048,576 cells on periodic faces, inlet or outlet (LBM_EINVAL
  *    beyond, use lbm_diag);
- *    the array costs every GPU that loads the library 4.5 MiB until exit.
+ *    the array costs every GPU that loads the library 6.75 MiB until exit.
  *  - region: device memory or NULL (host regions are rejected with LBM_EINVAL,
  *    since copying them would need scratch); out: host memory; synchronises.
  *  - The context's device must be current.  The first call on a device looks

@@ -608,7 +608,9 @@ __device__ __noinline__ void adjoint_general(const AdjParams& A, int p, uint32_t
     adjoint_cell<Q, T, false>(A, p, mask, park, lampark, dpark, jv);
 }
 
-// Dynamic shared memory of adjoint_kernel: three Q x kBlock float arrays.
+// Dynamic shared memory of adjoint_kernel: three Q x kBlock float arrays.  The
+// kernel is compiled for 512 resident threads per SM (128 registers), which
+// that shared memory allows (83 KB per 256 threads).
 template <int Q>
 constexpr size_t adjoint_smem_bytes()
 {
@@ -616,7 +618,7 @@ constexpr size_t adjoint_smem_bytes()
 }
 
 template <int Q, class T>
-__global__ void __launch_bounds__(kBlock, 2) adjoint_kernel(const AdjParams A)
+__global__ void __launch_bounds__(kBlock, 512 / kBlock) adjoint_kernel(const AdjParams A)
 {
     const Params& P = A.F;
     const int nbg = general_blocks(P);

@@ -405,8 +405,8 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     P.wide = wide ? 1 : 0;
     P.n_general = (int)c->general.size();
     // general cells per block: one warp's worth while the lean grid is under
-    // about four waves of 3 blocks on 152 SMs, full blocks beyond
-    P.gen_block = (c->n_store + kBlock - 1) / kBlock < 4 * 3 * 152 ? 32 : kBlock;
+    // about four waves of LBM_MIN_BLOCKS blocks on 152 SMs, full blocks beyond
+    P.gen_block = (c->n_store + kBlock - 1) / kBlock < 4 * LBM_MIN_BLOCKS * 152 ? 32 : kBlock;
     P.general = c->at<uint32_t>(c->L.general);
     P.rows = S.rows;
     P.rownb = c->at<int4>(c->L.rownb);
