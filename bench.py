@@ -131,16 +131,36 @@ class ClockSampler:
 
 
 def dist_setup():
+    """(world size, rank, local rank, torch.distributed or None) from the
+    launcher's environment; NCCL with GPUs, gloo without (host-side tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
 
-        backend = "nccl"
-        dist.init_process_group(backend)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         return ws, rank, local, dist
     return 1, 0, 0, None
+
+
+def max_over_ranks(dist, value, device):
+    """The largest value over all ranks, on every rank (the value itself
+    without a process group): the timed region of the slowest replica."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world_size, fluid_cells, time_steps, seconds):
+    """Whole-job fluid MLUPS: every rank advances its own replica of the
+    workload (weak scaling), timed by the slowest rank."""
+    return world_size * fluid_cells * time_steps / seconds / 1e6
 
 
 def flush_l2(torch, buf):
@@ -210,14 +230,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    total = sum(per)
-    if dist:
-        t = torch.tensor([total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(dist, sum(per), "cuda")
     clocks = clk.summary()
     launch_s = total / (args.steps * L)  # average step-kernel launch duration (back-to-back launches)
-    mlups = ws * nf * L * args.steps / total / 1e6
+    mlups = job_throughput(ws, nf, L * args.steps, total)
     bpu = bytes_per_update(WORKLOAD["q"], st0)
     achieved = bpu * nf / launch_s / 1e9
     traffic = load_traffic(name, st0)
