@@ -35,10 +35,20 @@ cudaError_t LBM_LAUNCHER(int what, const AdjParams& A, cudaStream_t s)
         const int grid = total_blocks(A.F);
         if (grid == 0) return cudaSuccess;
         constexpr size_t smem = adjoint_smem_bytes<LBM_Q>();
-        static const cudaError_t attr = cudaFuncSetAttribute(adjoint_kernel<LBM_Q, LBM_T>,
-                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        static const cudaError_t attr = [] {
+            const cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<LBM_Q, LBM_T, 512>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            return e != cudaSuccess ? e
+                                    : cudaFuncSetAttribute(adjoint_kernel<LBM_Q, LBM_T, 384>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        }();
         if (attr != cudaSuccess) return attr;
-        adjoint_kernel<LBM_Q, LBM_T><<<grid, kBlock, smem, s>>>(A);
+        // grids of up to two waves of the 512-thread variant (152 SMs) take
+        // the 384-thread one
+        if (grid <= 2 * 152 * (512 / kBlock))
+            adjoint_kernel<LBM_Q, LBM_T, 384><<<grid, kBlock, smem, s>>>(A);
+        else
+            adjoint_kernel<LBM_Q, LBM_T, 512><<<grid, kBlock, smem, s>>>(A);
     } else if (what == 1) {
         if (A.n_out == 0) return cudaSuccess;
         adjoint_outlet_fixup<LBM_Q><<<(A.n_out + 127) / 128, 128, 0, s>>>(A);
