@@ -203,7 +203,7 @@ lbm_status lbm_diag_noalloc(lbm_ctx* ctx, const uint8_t* region, double out[8]);
  *            eigendecomposition.
  *  - max_iter 1..1000, 0 <= tol < 1 (1e-6 and 16 converge to FP32 round-off
  *            for blood-flow drag).
- * FP32 storage only (LBM_EINVAL otherwise).  LBM_EINVAL when S is not finite
+ * Any storage type.  LBM_EINVAL when S is not finite
  * or not positive definite at a cell with phi < 1; LBM_ENOMEM when the buffer
  * is too small.  lbm_adjoint returns LBM_ESTATE while the tensor is set (its
  * reverse covers the explicit velocity solve only).  Synchronises the stream. */

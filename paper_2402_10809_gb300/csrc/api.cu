@@ -591,7 +591,6 @@ extern "C" lbm_status lbm_set_anisotropy(lbm_ctx* c, const float* shape, void* b
         c->base.aniso = nullptr;
         return LBM_OK;
     }
-    if (c->grid.storage != LBM_F32) return fail(c, LBM_EINVAL, "the anisotropic velocity solve needs FP32 storage");
     if (!buffer || reinterpret_cast<uintptr_t>(buffer) % 256 != 0)
         return fail(c, LBM_EINVAL, "anisotropy buffer null or not 256-byte aligned");
     if (bytes < lbm_anisotropy_buffer_size(c)) return fail(c, LBM_ENOMEM, "anisotropy buffer too small");

@@ -33,7 +33,6 @@ cudaError_t LBM_LAUNCHER(int mode, const Params& P, cudaStream_t s)
 {
     const int grid = total_blocks(P);
     if (grid == 0) return cudaSuccess;
-#if LBM_STORE == 0
     if (P.aniso) {
         switch (mode) {
             case kModeStep: lbm_kernel<LBM_Q, LBM_T, kModeStep, true><<<grid, kBlock, 0, s>>>(P); break;
@@ -42,9 +41,6 @@ cudaError_t LBM_LAUNCHER(int mode, const Params& P, cudaStream_t s)
         }
         return cudaGetLastError();
     }
-#else
-    if (P.aniso) return cudaErrorInvalidValue;  // the anisotropic solve is built for FP32 storage only
-#endif
     switch (mode) {
         case kModeStep: lbm_kernel<LBM_Q, LBM_T, kModeStep><<<grid, kBlock, 0, s>>>(P); break;
         case kModeMoments: lbm_kernel<LBM_Q, LBM_T, kModeMoments><<<grid, kBlock, 0, s>>>(P); break;

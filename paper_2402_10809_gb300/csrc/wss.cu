@@ -69,23 +69,30 @@ __global__ void __launch_bounds__(kBlock) wall_shear_kernel(const Params P, floa
     out[compact ? (long long)p : c.idx] = sqrtf(fmaf(tx, tx, fmaf(ty, ty, tz * tz)));
 }
 
+template <int Q, class T>
+void launch_wall_shear_t(const Params& P, float* out, int compact, int grid, cudaStream_t s)
+{
+    if (P.aniso)
+        wall_shear_kernel<Q, T, true><<<grid, kBlock, 0, s>>>(P, out, compact);
+    else
+        wall_shear_kernel<Q, T, false><<<grid, kBlock, 0, s>>>(P, out, compact);
+}
+
+template <int Q>
+cudaError_t launch_wall_shear_q(int storage, const Params& P, float* out, int compact, int grid, cudaStream_t s)
+{
+    if (storage == 0) launch_wall_shear_t<Q, float>(P, out, compact, grid, s);
+    else if (storage == 1) launch_wall_shear_t<Q, __half>(P, out, compact, grid, s);
+    else launch_wall_shear_t<Q, __nv_bfloat16>(P, out, compact, grid, s);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wall_shear(int q, int storage, const Params& P, float* out, int compact, cudaStream_t s)
 {
     const int grid = (P.n_store + kBlock - 1) / kBlock;
     if (grid == 0) return cudaSuccess;
-    if (P.aniso && storage != 0) return cudaErrorInvalidValue;  // anisotropic solve: FP32 storage only
-    if (q == 19) {
-        if (P.aniso) wall_shear_kernel<19, float, true><<<grid, kBlock, 0, s>>>(P, out, compact);
-        else if (storage == 0) wall_shear_kernel<19, float, false><<<grid, kBlock, 0, s>>>(P, out, compact);
-        else if (storage == 1) wall_shear_kernel<19, __half, false><<<grid, kBlock, 0, s>>>(P, out, compact);
-        else wall_shear_kernel<19, __nv_bfloat16, false><<<grid, kBlock, 0, s>>>(P, out, compact);
-    } else {
-        if (P.aniso) wall_shear_kernel<27, float, true><<<grid, kBlock, 0, s>>>(P, out, compact);
-        else if (storage == 0) wall_shear_kernel<27, float, false><<<grid, kBlock, 0, s>>>(P, out, compact);
-        else if (storage == 1) wall_shear_kernel<27, __half, false><<<grid, kBlock, 0, s>>>(P, out, compact);
-        else wall_shear_kernel<27, __nv_bfloat16, false><<<grid, kBlock, 0, s>>>(P, out, compact);
-    }
-    return cudaGetLastError();
+    if (q == 19) return launch_wall_shear_q<19>(storage, P, out, compact, grid, s);
+    return launch_wall_shear_q<27>(storage, P, out, compact, grid, s);
 }
 
 }  // namespace lbm

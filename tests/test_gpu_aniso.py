@@ -2,8 +2,8 @@
 iteration of the Sec. 3 remark) against the FP64 oracle.
 
 Error metric as in test_gpu_parity.py: max over fluid cells of |a - b| over
-max |b|.  Bounds: velocity 1e-5 and shear rate 1e-4 (FP32 storage, as for the
-isotropic path); the identity shape tensor reproduces the explicit isotropic
+max |b|.  Bounds: velocity 1e-5 and shear rate 1e-4 with FP32 storage, 1e-3 /
+2e-3 with FP16 deviations, 1e-2 / 2e-2 with BF16 (as for the isotropic path); the identity shape tensor reproduces the explicit isotropic
 GPU solution within 1e-6 (the same kernels up to the FP32 solve); the uniform
 periodic medium reaches the exact Darcy-Forchheimer fixed point within 1e-5.
 """
@@ -22,11 +22,11 @@ def rel_err(a, b, fluid):
     return np.abs(a[..., fluid].astype(np.float64) - b[..., fluid]).max() / np.abs(b[..., fluid]).max()
 
 
-@pytest.mark.parametrize("q", [19, 27])
-def test_aneurysm_against_oracle(lbm, q):
+@pytest.mark.parametrize("q,storage", [(19, "f32"), (27, "f32"), (27, "f16dev"), (27, "bf16dev")])
+def test_aneurysm_against_oracle(lbm, q, storage):
     prob = aneurysm_problem(24, q=q, small=True, u0=0.05, period=100.0)
     S = coil_shape_tensor(prob.flags.shape, ratio=4.0, seed=1)
-    sim = lbm.Simulation(prob)
+    sim = lbm.Simulation(prob, storage=storage)
     sim.set_anisotropy(S)
     sim.step(200)
     g = sim.moments()
@@ -35,7 +35,8 @@ def test_aneurysm_against_oracle(lbm, q):
     r = o.moments()
     fluid = prob.flags > 0
     eu, eg = rel_err(g["u"], r["u"], fluid), rel_err(g["gdot"], r["gdot"], fluid)
-    assert eu <= 1e-5 and eg <= 1e-4, (eu, eg)
+    bu, bg = {"f32": (1e-5, 1e-4), "f16dev": (1e-3, 2e-3), "bf16dev": (1e-2, 2e-2)}[storage]
+    assert eu <= bu and eg <= bg, (eu, eg)
     # the anisotropy changes the flow measurably
     iso = Oracle(prob)
     iso.step(200)
@@ -127,7 +128,3 @@ def test_errors(lbm):
     assert e.value.status == lbm.LBM_ESTATE
     sim.set_anisotropy(None)
     lbm.lbm_adjoint(sim.ctx, 4, 2, 0, region.ctypes.data, 0, ws.data_ptr(), nbytes, grad.data_ptr())
-    h = lbm.Simulation(prob, storage="f16dev")
-    with pytest.raises(lbm.LBMError) as e:
-        h.set_anisotropy(S)
-    assert e.value.status == lbm.LBM_EINVAL
