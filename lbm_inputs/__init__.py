@@ -35,7 +35,7 @@ from .configs import (  # noqa: F401
     coil_problem,
     channel_problem,
     periodic_box_problem,
-    BASELINE_CY,
+    WORKLOAD_CY,
     ANEURYSM_LAMBDA,
     PAPER_TABLE1,
 )

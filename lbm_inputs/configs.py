@@ -19,7 +19,7 @@ from . import porosity as por
 PAPER_TABLE1 = dict(rho0=1060.0, dx=43.95e-6, dt=5.42e-6, d_p=600e-6)
 
 # Carreau-Yasuda blood parameters of the synthetic workloads (SI).
-BASELINE_CY = dict(mu0=0.056, mu_inf=0.00345, lam=3.313, n=0.3568, a=2.0)
+WORKLOAD_CY = dict(mu0=0.056, mu_inf=0.00345, lam=3.313, n=0.3568, a=2.0)
 
 # Viscosity relaxation time of the aneurysm workloads [s].  With lam = 3.313 s
 # (611 255 time steps at the Table 1 spacing) the discrete scheme loses
@@ -28,11 +28,11 @@ BASELINE_CY = dict(mu0=0.056, mu_inf=0.00345, lam=3.313, n=0.3568, a=2.0)
 # does too.  lam / 100 stays finite (384^3 over 2000 steps in all three storage
 # types, 512^3 over 5000 steps), and it keeps the whole viscosity range of the
 # law in play (omega from 1.05 to 1.89).
-ANEURYSM_LAMBDA = BASELINE_CY["lam"] / 100
+ANEURYSM_LAMBDA = WORKLOAD_CY["lam"] / 100
 
 # Body force (lattice units) driving the 32x32x64 pipe: the Newtonian estimate
 # G = 4 Re nu_inf^2 / R^3 for Re = 10, R = 14 and nu_inf = 0.0091326 (mu_inf of
-# BASELINE_CY at the Table 1 spacing).
+# WORKLOAD_CY at the Table 1 spacing).
 PIPE_BODY_FORCE = 1.2158e-6
 
 
@@ -73,7 +73,7 @@ def pipe_problem(q=19, storage="f32"):
     phi = por.plug_porosity(flags)
     bc = _no_inlet()
     bc["body_force"] = (0.0, 0.0, PIPE_BODY_FORCE)
-    rheo = dict(BASELINE_CY, rho0=PAPER_TABLE1["rho0"], dx=PAPER_TABLE1["dx"], dt=PAPER_TABLE1["dt"])
+    rheo = dict(WORKLOAD_CY, rho0=PAPER_TABLE1["rho0"], dx=PAPER_TABLE1["dx"], dt=PAPER_TABLE1["dt"])
     porous = dict(d_p=PAPER_TABLE1["d_p"], k_const=0.0, nu_darcy=0.0, forchheimer=1)
     return Problem("pipe32x32x64", flags, phi, q, (0, 0, 1), rheo, porous, bc, None)
 
@@ -98,7 +98,7 @@ def aneurysm_problem(n, q=27, seed=0, small=False, porous_sac=True, u0=0.05, amp
     bc = dict(body_force=(0.0, 0.0, 0.0), inlet_axis=2, inlet_side=0,
               inlet_center=(cx, cy, 0.0), inlet_radius=r, u0=u0, amp=amp, period=period,
               ramp_steps=ramp_steps, outlet_axis=0, outlet_side=1, rho_out=1.0)
-    rheo = dict(BASELINE_CY, rho0=PAPER_TABLE1["rho0"], dx=PAPER_TABLE1["dx"], dt=PAPER_TABLE1["dt"])
+    rheo = dict(WORKLOAD_CY, rho0=PAPER_TABLE1["rho0"], dx=PAPER_TABLE1["dx"], dt=PAPER_TABLE1["dt"])
     rheo["lam"] = ANEURYSM_LAMBDA if lam is None else lam
     porous = dict(d_p=PAPER_TABLE1["d_p"], k_const=0.0, nu_darcy=0.0, forchheimer=1)
     name = f"aneurysm{n}" + ("s" if small else "")
