@@ -51,9 +51,10 @@ def test_pipe_fp32_200_steps(lbm, q):
 
 
 def test_small_aneurysm_workload_relaxation_time(lbm):
-    """The 24^3 aneurysm with the workload description's lambda = 3.313 s (the
-    aneurysm family defaults to lambda / 100, see lbm_inputs.configs; at 24^3 the
-    original value stays finite over 200 steps): the strongest shear thinning."""
+    """The 24^3 aneurysm with the blood relaxation time lambda = 3.313 s of
+    WORKLOAD_CY (the aneurysm family defaults to lambda / 100, see
+    lbm_inputs.configs; at 24^3 the full value stays finite over 200 steps):
+    the strongest shear thinning."""
     from lbm_inputs.configs import WORKLOAD_CY
 
     prob = aneurysm_problem(24, q=27, small=True, u0=0.05, period=100.0, lam=WORKLOAD_CY["lam"])
