@@ -125,3 +125,14 @@ def test_porosity_average_host_checks():
     assert call(work=257) == lbm.LBM_EINVAL
     assert call(nbytes=ws - 1) == lbm.LBM_ENOMEM
     assert call(dims=(0, 8, 8)) == lbm.LBM_EINVAL
+
+
+def test_anisotropy_entry_points_host_checks():
+    """lbm_set_anisotropy / lbm_anisotropy_buffer_size without a context: the
+    checks that return before any device work."""
+    from paper_2402_10809_gb300 import lbm
+
+    L = lbm.load()
+    assert L.lbm_anisotropy_buffer_size(None) == 0
+    assert L.lbm_set_anisotropy(None, C.c_void_p(256), C.c_void_p(256), 1 << 20, 16, C.c_float(1e-6)) == lbm.LBM_EINVAL
+    assert L.lbm_set_anisotropy(None, None, None, 0, 16, C.c_float(1e-6)) == lbm.LBM_EINVAL
