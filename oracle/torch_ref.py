@@ -50,9 +50,12 @@ def _safe_norm(s):
 
 
 class TorchLBM:
-    """Whole-grid FP64 LBM for one lbm_inputs.Problem."""
+    """Whole-grid FP64 LBM for one lbm_inputs.Problem.  ``shape_tensor``: the
+    optional (6, nz, ny, nx) SPD tensor S (xx yy zz xy xz yz) of an anisotropic
+    permeability K = k(phi) S^{-1}, solved by the fixed-point iteration of the
+    Sec. 3 remark."""
 
-    def __init__(self, prob):
+    def __init__(self, prob, shape_tensor=None):
         self.prob = prob
         nx, ny, nz = prob.dims
         self.n = (nx, ny, nz)
@@ -78,6 +81,16 @@ class TorchLBM:
         self.fluid = flags != SOLID
         self.periodic = prob.periodic
         self._build_links()
+        self.S = self.Sh = None
+        if shape_tensor is not None:
+            s = torch.tensor(np.asarray(shape_tensor, dtype=np.float64))
+            M = torch.empty(s.shape[1:] + (3, 3), dtype=torch.float64)
+            for (a, b), k in (((0, 0), 0), ((1, 1), 1), ((2, 2), 2), ((0, 1), 3), ((0, 2), 4), ((1, 2), 5)):
+                M[..., a, b] = s[k]
+                M[..., b, a] = s[k]
+            lam, V = torch.linalg.eigh(M)
+            self.S = M  # [..., 3, 3]
+            self.Sh = V @ torch.diag_embed(torch.sqrt(lam)) @ V.transpose(-1, -2)
 
     # ------------------------------------------------------------ geometry
     def _shift(self, t, d):
@@ -150,6 +163,9 @@ class TorchLBM:
         v = (m + 0.5 * rho * self.g) / (phi * rho)
         vn = _safe_norm((v * v).sum(0))
         inv_k, inv_sk, cf = self.closure(phi)
+        if self.S is not None:
+            u, fd = self._anisotropic(v, phi, inv_k, inv_sk, cf)
+            return rho, u, rho * (self.g + fd)
         c0 = 0.5 + phi * self.nu_d * inv_k / 4
         c1 = phi ** 2 * cf * inv_sk / 2
         u = v / (c0 + torch.sqrt(c0 * c0 + c1 * vn))
@@ -157,6 +173,32 @@ class TorchLBM:
         fd = -(phi ** 2) * self.nu_d * inv_k * u - phi ** 3 * cf * inv_sk * un * u
         F = rho * (self.g + fd)
         return rho, u, F
+
+    def _anisotropic(self, v, phi, inv_k, inv_sk, cf):
+        """Velocity and drag with K^{-1} = S / k, K^{-1/2} = S^{1/2} / sqrt(k):
+        (A + |u| B) u = v, A = Id + (phi nu / 2) K^{-1},
+        B = (phi^2 C_F / 2) K^{-1/2}, by u_{m+1} = (A + |u_m| B)^{-1} v from
+        u_0 = v, batched 3x3 solves over the grid (cells without a medium have
+        K^{-1} = 0, hence u = v); f(u) = -phi^2 nu K^{-1} u -
+        phi^3 C_F |u| K^{-1/2} u."""
+        e = (...,) + (None, None)
+        Kinv = self.S * inv_k[e]
+        Kinvh = self.Sh * inv_sk[e]
+        A = torch.eye(3, dtype=torch.float64) + (phi * self.nu_d / 2)[e] * Kinv
+        B = (phi ** 2 * cf / 2)[e] * Kinvh
+        vv = v.permute(1, 2, 3, 0).unsqueeze(-1)  # [..., 3, 1]
+        u = vv
+        scale = vv.abs().max()
+        for _ in range(200):
+            un = torch.sqrt((u * u).sum((-2, -1)))
+            u_new = torch.linalg.solve(A + un[e] * B, vv)
+            done = bool((u_new - u).abs().max() <= 1e-15 * scale)
+            u = u_new
+            if done:
+                break
+        un = torch.sqrt((u * u).sum((-2, -1)))
+        fd = -(phi ** 2 * self.nu_d)[e] * (Kinv @ u) - (phi ** 3 * cf)[e] * un[e] * (Kinvh @ u)
+        return u.squeeze(-1).permute(3, 0, 1, 2), fd.squeeze(-1).permute(3, 0, 1, 2)
 
     def equilibrium(self, phi, rho, u):
         cu = torch.einsum("qa,a...->q...", self.cf, u)

@@ -14,11 +14,11 @@ from oracle.oracle import Oracle
 from oracle.torch_ref import TorchLBM
 
 
-def _compare(prob, steps):
-    o = Oracle(prob)
+def _compare(prob, steps, shape_tensor=None):
+    o = Oracle(prob, shape_tensor=shape_tensor)
     o.step(steps)
     m = o.moments()
-    tl = TorchLBM(prob)
+    tl = TorchLBM(prob, shape_tensor=shape_tensor)
     phi = torch.tensor(prob.phi.astype(np.float64))
     f, om = tl.run(phi, steps)
     fl = tl.fields(f, om, phi)
@@ -35,6 +35,16 @@ def test_c_and_torch_oracles_agree_on_small_aneurysm(q):
     """Porous sac, Carreau-Yasuda, pulsatile Zou-He inlet, extrapolation outlet."""
     prob = aneurysm_problem(24, q=q, small=True, u0=0.05, period=40.0)
     _compare(prob, 25)
+
+
+def test_c_and_torch_oracles_agree_with_anisotropic_permeability():
+    """The fixed-point velocity solve with a per-cell shape tensor: Gaussian
+    elimination and an eigendecomposition square root in C + numpy against
+    batched torch solves and torch's own eigendecomposition."""
+    from lbm_inputs import coil_shape_tensor
+
+    prob = aneurysm_problem(24, q=27, small=True, u0=0.05, period=40.0)
+    _compare(prob, 25, shape_tensor=coil_shape_tensor(prob.flags.shape, ratio=4.0, seed=1))
 
 
 def test_c_and_torch_oracles_agree_on_pipe():
