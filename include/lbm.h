@@ -205,8 +205,10 @@ lbm_status lbm_diag_noalloc(lbm_ctx* ctx, const uint8_t* region, double out[8]);
  *            for blood-flow drag).
  * Any storage type.  LBM_EINVAL when S is not finite
  * or not positive definite at a cell with phi < 1; LBM_ENOMEM when the buffer
- * is too small.  lbm_adjoint returns LBM_ESTATE while the tensor is set (its
- * reverse covers the explicit velocity solve only).  Synchronises the stream. */
+ * is too small.  lbm_adjoint differentiates the anisotropic solve too (the
+ * implicit-function reverse of its converged velocity, with the porosity
+ * dependence of the closure; S itself is held fixed).  Synchronises the
+ * stream. */
 size_t lbm_anisotropy_buffer_size(const lbm_ctx* ctx);
 lbm_status lbm_set_anisotropy(lbm_ctx* ctx, const float* shape, void* buffer, size_t bytes, int32_t max_iter,
                               float tol);

@@ -91,6 +91,13 @@ class TorchLBM:
             lam, V = torch.linalg.eigh(M)
             self.S = M  # [..., 3, 3]
             self.Sh = V @ torch.diag_embed(torch.sqrt(lam)) @ V.transpose(-1, -2)
+            # the tensor acts where there is a medium (phi < 1, the reading of
+            # the C oracle); cells with phi = 1 keep the isotropic closure,
+            # which also fixes the one-sided derivative there
+            medium = torch.tensor(np.asarray(prob.phi) < 1)[..., None, None]
+            eye = torch.eye(3, dtype=torch.float64)
+            self.S = torch.where(medium, self.S, eye)
+            self.Sh = torch.where(medium, self.Sh, eye)
 
     # ------------------------------------------------------------ geometry
     def _shift(self, t, d):
@@ -190,13 +197,13 @@ class TorchLBM:
         u = vv
         scale = vv.abs().max()
         for _ in range(200):
-            un = torch.sqrt((u * u).sum((-2, -1)))
+            un = _safe_norm((u * u).sum((-2, -1)))
             u_new = torch.linalg.solve(A + un[e] * B, vv)
             done = bool((u_new - u).abs().max() <= 1e-15 * scale)
             u = u_new
             if done:
                 break
-        un = torch.sqrt((u * u).sum((-2, -1)))
+        un = _safe_norm((u * u).sum((-2, -1)))
         fd = -(phi ** 2 * self.nu_d)[e] * (Kinv @ u) - (phi ** 3 * cf)[e] * un[e] * (Kinvh @ u)
         return u.squeeze(-1).permute(3, 0, 1, 2), fd.squeeze(-1).permute(3, 0, 1, 2)
 

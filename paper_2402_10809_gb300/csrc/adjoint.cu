@@ -36,19 +36,30 @@ cudaError_t LBM_LAUNCHER(int what, const AdjParams& A, cudaStream_t s)
         if (grid == 0) return cudaSuccess;
         constexpr size_t smem = adjoint_smem_bytes<LBM_Q>();
         static const cudaError_t attr = [] {
-            const cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<LBM_Q, LBM_T, 512>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            return e != cudaSuccess ? e
-                                    : cudaFuncSetAttribute(adjoint_kernel<LBM_Q, LBM_T, 384>,
-                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            const void* k[4] = {(const void*)adjoint_kernel<LBM_Q, LBM_T, 512, false>,
+                                (const void*)adjoint_kernel<LBM_Q, LBM_T, 384, false>,
+                                (const void*)adjoint_kernel<LBM_Q, LBM_T, 512, true>,
+                                (const void*)adjoint_kernel<LBM_Q, LBM_T, 384, true>};
+            for (const void* f : k) {
+                const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
         }();
         if (attr != cudaSuccess) return attr;
         // grids of up to two waves of the 512-thread variant (152 SMs) take
         // the 384-thread one
-        if (grid <= 2 * 152 * (512 / kBlock))
-            adjoint_kernel<LBM_Q, LBM_T, 384><<<grid, kBlock, smem, s>>>(A);
-        else
-            adjoint_kernel<LBM_Q, LBM_T, 512><<<grid, kBlock, smem, s>>>(A);
+        const bool small = grid <= 2 * 152 * (512 / kBlock);
+        if (A.F.aniso) {
+            if (small)
+                adjoint_kernel<LBM_Q, LBM_T, 384, true><<<grid, kBlock, smem, s>>>(A);
+            else
+                adjoint_kernel<LBM_Q, LBM_T, 512, true><<<grid, kBlock, smem, s>>>(A);
+        } else if (small) {
+            adjoint_kernel<LBM_Q, LBM_T, 384, false><<<grid, kBlock, smem, s>>>(A);
+        } else {
+            adjoint_kernel<LBM_Q, LBM_T, 512, false><<<grid, kBlock, smem, s>>>(A);
+        }
     } else if (what == 1) {
         if (A.n_out == 0) return cudaSuccess;
         adjoint_outlet_fixup<LBM_Q><<<(A.n_out + 127) / 128, 128, 0, s>>>(A);

@@ -151,6 +151,86 @@ __device__ __forceinline__ float macro_adjoint(const Params& P, float phi, float
     return b.sd;
 }
 
+// Reverse of macroscopic_aniso() at a cell with phi < 1, same interface as
+// macro_adjoint.  Forward: v = m / sigma + g / (2 phi); u solves
+// G(u) = (Id + Ah + |u| B) u - v = 0 with Ah = a(phi) S, B = b(phi) S^{1/2}
+// (a = 2 alpha, b = C1 of the isotropic closure); F = rho g - 2 sigma w,
+// w = Ah u + |u| B u.  Reverse: wbar = -2 sigma Fbar; ubar gains
+// Ah wbar + |u| B wbar + (wbar . B u) u / |u|; the implicit function gives
+// vbar = lambda with J^T lambda = ubar, J = dG/du = Id + Ah + |u| B + (B u) u^T / |u|;
+// phi enters through a and b: phibar += (a'/a) (wbar - lambda) . Ah u +
+// (b'/b) |u| (wbar - lambda) . B u (Ah u / a = S u, B u / b = S^{1/2} u).
+__device__ __forceinline__ float macro_adjoint_aniso(const Params& P, int p, float phi, float mx, float my, float mz,
+                                                     const Macro& M, MacroBar b, float& mbx, float& mby, float& mbz,
+                                                     float& phib)
+{
+    const float iphi = __frcp_rn(phi);
+    const float isig = __fdividef(1.0f, M.sigma);
+    const size_t n = (size_t)P.n_store;
+    const float* q = P.aniso + p;
+    const float axx = __ldg(q), ayy = __ldg(q + n), azz = __ldg(q + 2 * n);
+    const float axy = __ldg(q + 3 * n), axz = __ldg(q + 4 * n), ayz = __ldg(q + 5 * n);
+    const float bxx = __ldg(q + 6 * n), byy = __ldg(q + 7 * n), bzz = __ldg(q + 8 * n);
+    const float bxy = __ldg(q + 9 * n), bxz = __ldg(q + 10 * n), byz = __ldg(q + 11 * n);
+    const float ux = M.ux, uy = M.uy, uz = M.uz;
+    const float un = sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+    const float iun = un > 0.0f ? __fdividef(1.0f, un) : 0.0f;
+    const float hx = ux * iun, hy = uy * iun, hz = uz * iun;
+    // A u and B u
+    const float Aux = fmaf(axx, ux, fmaf(axy, uy, axz * uz));
+    const float Auy = fmaf(axy, ux, fmaf(ayy, uy, ayz * uz));
+    const float Auz = fmaf(axz, ux, fmaf(ayz, uy, azz * uz));
+    const float Bux = fmaf(bxx, ux, fmaf(bxy, uy, bxz * uz));
+    const float Buy = fmaf(bxy, ux, fmaf(byy, uy, byz * uz));
+    const float Buz = fmaf(bxz, ux, fmaf(byz, uy, bzz * uz));
+    const float wx = fmaf(un, Bux, Aux), wy = fmaf(un, Buy, Auy), wz = fmaf(un, Buz, Auz);
+    // F = rho g - 2 sigma w
+    b.rho += fmaf(b.Fx, P.gx, fmaf(b.Fy, P.gy, b.Fz * P.gz));
+    b.sigma -= 2.0f * fmaf(b.Fx, wx, fmaf(b.Fy, wy, b.Fz * wz));
+    const float wbx = -2.0f * M.sigma * b.Fx, wby = -2.0f * M.sigma * b.Fy, wbz = -2.0f * M.sigma * b.Fz;
+    // ubar += A wbar + |u| B wbar + (wbar . B u) u / |u|
+    const float wBu = fmaf(wbx, Bux, fmaf(wby, Buy, wbz * Buz));
+    const float ubx = b.ux + fmaf(axx, wbx, fmaf(axy, wby, axz * wbz)) +
+                      fmaf(un, fmaf(bxx, wbx, fmaf(bxy, wby, bxz * wbz)), wBu * hx);
+    const float uby = b.uy + fmaf(axy, wbx, fmaf(ayy, wby, ayz * wbz)) +
+                      fmaf(un, fmaf(bxy, wbx, fmaf(byy, wby, byz * wbz)), wBu * hy);
+    const float ubz = b.uz + fmaf(axz, wbx, fmaf(ayz, wby, azz * wbz)) +
+                      fmaf(un, fmaf(bxz, wbx, fmaf(byz, wby, bzz * wbz)), wBu * hz);
+    // J^T = Id + A + |u| B + h (B u)^T: element (r, c) = sym(r, c) + h_r (Bu)_c
+    const float j00 = 1.0f + fmaf(un, bxx, axx) + hx * Bux, j01 = fmaf(un, bxy, axy) + hx * Buy,
+                j02 = fmaf(un, bxz, axz) + hx * Buz;
+    const float j10 = fmaf(un, bxy, axy) + hy * Bux, j11 = 1.0f + fmaf(un, byy, ayy) + hy * Buy,
+                j12 = fmaf(un, byz, ayz) + hy * Buz;
+    const float j20 = fmaf(un, bxz, axz) + hz * Bux, j21 = fmaf(un, byz, ayz) + hz * Buy,
+                j22 = 1.0f + fmaf(un, bzz, azz) + hz * Buz;
+    // lambda = (J^T)^{-1} ubar by the adjugate
+    const float c00 = fmaf(j11, j22, -j12 * j21), c01 = fmaf(j02, j21, -j01 * j22), c02 = fmaf(j01, j12, -j02 * j11);
+    const float c10 = fmaf(j12, j20, -j10 * j22), c11 = fmaf(j00, j22, -j02 * j20), c12 = fmaf(j02, j10, -j00 * j12);
+    const float c20 = fmaf(j10, j21, -j11 * j20), c21 = fmaf(j01, j20, -j00 * j21), c22 = fmaf(j00, j11, -j01 * j10);
+    const float idet = __frcp_rn(fmaf(j00, c00, fmaf(j01, c10, j02 * c20)));
+    const float lx = fmaf(c00, ubx, fmaf(c01, uby, c02 * ubz)) * idet;
+    const float ly = fmaf(c10, ubx, fmaf(c11, uby, c12 * ubz)) * idet;
+    const float lz = fmaf(c20, ubx, fmaf(c21, uby, c22 * ubz)) * idet;
+    // phi through a(phi) = 2 alpha and b(phi) = C1
+    float k1, k2, dalpha, dc1;
+    darcy_coeffs(P, phi, iphi, k1, k2);
+    darcy_derivs(P, phi, iphi, dalpha, dc1);
+    const float alpha = 0.25f * k1 * iphi, c1 = 0.5f * k2 * iphi;
+    const float dx = wbx - lx, dy = wby - ly, dz = wbz - lz;
+    if (alpha > 0.0f) phib = fmaf(__fdividef(dalpha, alpha), fmaf(dx, Aux, fmaf(dy, Auy, dz * Auz)), phib);
+    if (c1 > 0.0f) phib = fmaf(__fdividef(dc1, c1) * un, fmaf(dx, Bux, fmaf(dy, Buy, dz * Buz)), phib);
+    // v = m / sigma + g / (2 phi)
+    mbx = lx * isig;
+    mby = ly * isig;
+    mbz = lz * isig;
+    b.sigma -= fmaf(lx, mx, fmaf(ly, my, lz * mz)) * isig * isig;
+    phib -= 0.5f * fmaf(lx, P.gx, fmaf(ly, P.gy, lz * P.gz)) * iphi * iphi;
+    const float rd = (b.rho + b.drho) * iphi;
+    b.sd += b.sigma + rd;
+    phib += b.sigma - rd * M.drho;
+    return b.sd;
+}
+
 // Reverse of zou_he() in place on park (adjoints of the populations after the
 // boundary condition in, adjoints of the pulled populations out; the unknown
 // slots end at zero).  The condition is affine in the pulled populations and
@@ -295,7 +375,7 @@ __device__ __forceinline__ void outlet_adjoint(const AdjParams& A, const Coords&
 // its pull sources), all filled by asynchronous copies issued at the start so
 // that their latencies overlap; the per-cell scalars are loaded before any
 // wait for the same reason.
-template <int Q, class T, bool fast>
+template <int Q, class T, bool fast, bool AN>
 __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t mask, volatile float* park,
                                              volatile float* lampark, volatile float* dpark, double& jv)
 {
@@ -372,7 +452,10 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
         smx = m.mx;
         smy = m.my;
         smz = m.mz;
-        M = macroscopic(P, phi, m.sd, m.mx, m.my, m.mz);
+        if constexpr (AN)
+            M = macroscopic_aniso(P, p, phi, m.sd, m.mx, m.my, m.mz);
+        else
+            M = macroscopic(P, phi, m.sd, m.mx, m.my, m.mz);
         const float sd3 = M.sd * (1.0f / 3.0f);
         pxx = fmaf(M.ux, fmaf(-M.sigma, M.ux, M.Fx), m.sxx - sd3);
         pyy = fmaf(M.uy, fmaf(-M.sigma, M.uy, M.Fy), m.syy - sd3);
@@ -539,7 +622,11 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
         b.sd -= (bxx + byy + bzz) * (1.0f / 3.0f);
     }
     float mbx, mby, mbz;
-    const float sdb = macro_adjoint(P, phi, smx, smy, smz, M, b, mbx, mby, mbz, phib);
+    float sdb;
+    if (AN && phi < 1.0f)
+        sdb = macro_adjoint_aniso(P, p, phi, smx, smy, smz, M, b, mbx, mby, mbz, phib);
+    else
+        sdb = macro_adjoint(P, phi, smx, smy, smz, M, b, mbx, mby, mbz, phib);
 
     // ---- adjoints of the populations after the boundary condition:
     // gbar_i = (1 - omega) a_i + sdbar + mbar.c_i + c_i^T Pibar c_i (a = 0 at t = T)
@@ -601,11 +688,11 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
     A.gphi[p] = gphi0 + gacc;
 }
 
-template <int Q, class T>
+template <int Q, class T, bool AN>
 __device__ __noinline__ void adjoint_general(const AdjParams& A, int p, uint32_t mask, volatile float* park,
                                              volatile float* lampark, volatile float* dpark, double& jv)
 {
-    adjoint_cell<Q, T, false>(A, p, mask, park, lampark, dpark, jv);
+    adjoint_cell<Q, T, false, AN>(A, p, mask, park, lampark, dpark, jv);
 }
 
 // Dynamic shared memory of adjoint_kernel: three Q x kBlock float arrays.  The
@@ -621,8 +708,9 @@ constexpr size_t adjoint_smem_bytes()
 // registers, some spills) hides more latency on large grids; 384 (168
 // registers, no spills) runs each cell faster, which wins when the grid is
 // only one or two waves (measured: 47.9 against 52.1 us per reverse step at
-// 128^3, 140 against 128 us at 256^3).
-template <int Q, class T, int TPS>
+// 128^3, 140 against 128 us at 256^3).  AN: the reverse of the anisotropic
+// velocity solve at cells with phi < 1.
+template <int Q, class T, int TPS, bool AN>
 __global__ void __launch_bounds__(kBlock, TPS / kBlock) adjoint_kernel(const AdjParams A)
 {
     const Params& P = A.F;
@@ -636,7 +724,7 @@ __global__ void __launch_bounds__(kBlock, TPS / kBlock) adjoint_kernel(const Adj
         const int k = (int)blockIdx.x * P.gen_block + (int)threadIdx.x;
         if ((int)threadIdx.x < P.gen_block && k < P.n_general) {
             const int p = (int)P.general[k];
-            adjoint_general<Q, T>(A, p, P.mask[p], park, lampark, dpark, jv);
+            adjoint_general<Q, T, AN>(A, p, P.mask[p], park, lampark, dpark, jv);
         }
     } else {
         const int p = ((int)blockIdx.x - nbg) * kBlock + (int)threadIdx.x;
@@ -644,7 +732,7 @@ __global__ void __launch_bounds__(kBlock, TPS / kBlock) adjoint_kernel(const Adj
             const uint32_t mask = P.mask[p];
             // ghost slots hold no state; general cells belong to the general blocks
             if (!(mask & (kGhostBit | kGeneralBits)) && !P.wide)
-                adjoint_cell<Q, T, true>(A, p, mask, park, lampark, dpark, jv);
+                adjoint_cell<Q, T, true, AN>(A, p, mask, park, lampark, dpark, jv);
         }
     }
     if (A.objective) {

@@ -802,8 +802,6 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, int32_t obje
     if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
     if (T < 1 || K < 1) return fail(c, LBM_EINVAL, "T and K must be >= 1");
     if (objective != 0 && objective != 1) return fail(c, LBM_EINVAL, "objective must be 0 (kinetic energy) or 1 (wall shear)");
-    if (c->base.aniso)
-        return fail(c, LBM_ESTATE, "the adjoint does not cover the anisotropic velocity solve (lbm_set_anisotropy)");
     if (!region || !workspace || !grad || !J) return fail(c, LBM_EINVAL, "null pointer argument");
     if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
         return fail(c, LBM_EINVAL, "adjoint workspace not 256-byte aligned");
