@@ -150,3 +150,49 @@ def test_wall_shear_objective_gradient_matches_differences():
             vals.append(float(tl.objective(torch.tensor(ph), T, prob.region, checkpoint=False, kind="wss")))
         fd = (vals[0] - vals[1]) / 2e-5
         assert abs(fd - grad[z, y, x]) <= 1e-4 * scale, (fd, grad[z, y, x])
+
+
+def test_anisotropic_reference_gradient_matches_finite_differences():
+    """With a shape tensor: d J / d phi from autograd of the torch restatement
+    (the fixed-point iteration unrolled to FP64 convergence) against central
+    differences (eps = 1e-4) of the C oracle's objective, at sac voxels of the
+    porous medium and at the largest-gradient voxel."""
+    from lbm_inputs import coil_shape_tensor
+
+    prob = aneurysm_problem(24, q=27, small=True, u0=0.05, period=50.0)
+    S = coil_shape_tensor(prob.flags.shape, ratio=4.0, seed=1)
+    T = 16
+    J, grad = TorchLBM(prob, shape_tensor=S).gradient(prob.phi, T, prob.region)
+    J0 = Oracle(prob, shape_tensor=S).run_objective(T, prob.region)
+    assert abs(J - J0) < 1e-12 * abs(J0)
+    rng = np.random.default_rng(2)
+    cand = np.argwhere((prob.region > 0) & (prob.flags > 0) & (prob.phi < 0.99) & (prob.phi > 0.61))
+    pts = list(cand[rng.choice(len(cand), 4, replace=False)])
+    big = np.unravel_index(np.argmax(np.abs(np.where(prob.phi < 0.99, grad, 0.0))), grad.shape)
+    pts.append(np.array(big))
+    scale = np.abs(grad).max()
+    eps = 1e-4
+    for z, y, x in pts:
+        ph = prob.phi.astype(np.float64).copy()
+        ph[z, y, x] += eps
+        jp = Oracle(prob, phi=ph, shape_tensor=S).run_objective(T, prob.region)
+        ph[z, y, x] -= 2 * eps
+        jm = Oracle(prob, phi=ph, shape_tensor=S).run_objective(T, prob.region)
+        fd = (jp - jm) / (2 * eps)
+        assert abs(fd - grad[z, y, x]) < 1e-4 * scale + 1e-6 * abs(fd), (z, y, x, fd, grad[z, y, x])
+
+
+def test_c_and_torch_wall_shear_agree_with_anisotropic_permeability():
+    from lbm_inputs import coil_shape_tensor
+
+    prob = aneurysm_problem(24, q=27, small=True, u0=0.05, period=100.0)
+    S = coil_shape_tensor(prob.flags.shape, ratio=4.0, seed=1)
+    tl = TorchLBM(prob, shape_tensor=S)
+    phi = torch.tensor(prob.phi.astype(np.float64))
+    f, om = tl.run(phi, 30)
+    wt = tl.wall_shear(f, om, phi).numpy()
+    o = Oracle(prob, shape_tensor=S)
+    o.step(30)
+    wo = o.wall_shear()
+    assert np.array_equal(wt > 0, wo > 0)
+    assert np.abs(wt - wo).max() <= 1e-12 * np.abs(wo).max()
