@@ -35,53 +35,63 @@ class OracleParams(C.Structure):
     ]
 
 
+def compile_library(src, out):
+    """Compile one C oracle source into the shared library ``out`` (gcc, OpenMP)."""
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-D_GNU_SOURCE",
+           "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force=False):
     """Compile the oracle into oracle/_build/liboracle.so (gcc, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
-    tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-D_GNU_SOURCE",
-           "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    return compile_library(_SRC, _LIB)
+
+
+def load_library(path):
+    """ctypes handle of a compiled oracle library with its signatures declared."""
+    L = C.CDLL(path)
+    P = C.POINTER
+    d = P(C.c_double)
+    L.oracle_create.restype = C.c_void_p
+    L.oracle_create.argtypes = [P(OracleParams), P(C.c_uint8), d, P(C.c_int32)]
+    L.oracle_destroy.argtypes = [C.c_void_p]
+    L.oracle_step.argtypes = [C.c_void_p, C.c_int64]
+    L.oracle_moments.argtypes = [C.c_void_p, d, d, d, d, d, d]
+    L.oracle_diag.argtypes = [C.c_void_p, P(C.c_uint8), d]
+    L.oracle_wss.restype = None
+    L.oracle_wss.argtypes = [C.c_void_p, C.c_void_p]
+    L.oracle_run_objective.restype = C.c_double
+    L.oracle_run_objective.argtypes = [C.c_void_p, C.c_int64, P(C.c_uint8)]
+    L.oracle_nfluid.restype = C.c_int64
+    L.oracle_nfluid.argtypes = [C.c_void_p]
+    L.oracle_time.restype = C.c_int64
+    L.oracle_time.argtypes = [C.c_void_p]
+    L.oracle_q.restype = C.c_int32
+    L.oracle_q.argtypes = [C.c_void_p]
+    L.oracle_lattice.argtypes = [C.c_void_p, P(C.c_int32), d, P(C.c_int32)]
+    L.oracle_cells.argtypes = [C.c_void_p, P(C.c_int64)]
+    L.oracle_get_state.argtypes = [C.c_void_p, d, d]
+    L.oracle_set_state.argtypes = [C.c_void_p, d, d, C.c_int64]
+    L.oracle_collide_cell.argtypes = [C.c_void_p, C.c_int64, d, C.c_double, d, d]
+    L.oracle_apply_boundaries.argtypes = [C.c_void_p, C.c_int64]
+    L.oracle_lattice_params.argtypes = [C.c_void_p, d]
+    L.oracle_num_threads.restype = C.c_int32
+    L.oracle_set_anisotropy.restype = C.c_int32
+    L.oracle_set_anisotropy.argtypes = [C.c_void_p, d, d]
+    return L
 
 
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            P = C.POINTER
-            d = P(C.c_double)
-            L.oracle_create.restype = C.c_void_p
-            L.oracle_create.argtypes = [P(OracleParams), P(C.c_uint8), d, P(C.c_int32)]
-            L.oracle_destroy.argtypes = [C.c_void_p]
-            L.oracle_step.argtypes = [C.c_void_p, C.c_int64]
-            L.oracle_moments.argtypes = [C.c_void_p, d, d, d, d, d, d]
-            L.oracle_diag.argtypes = [C.c_void_p, P(C.c_uint8), d]
-            L.oracle_wss.restype = None
-            L.oracle_wss.argtypes = [C.c_void_p, C.c_void_p]
-            L.oracle_run_objective.restype = C.c_double
-            L.oracle_run_objective.argtypes = [C.c_void_p, C.c_int64, P(C.c_uint8)]
-            L.oracle_nfluid.restype = C.c_int64
-            L.oracle_nfluid.argtypes = [C.c_void_p]
-            L.oracle_time.restype = C.c_int64
-            L.oracle_time.argtypes = [C.c_void_p]
-            L.oracle_q.restype = C.c_int32
-            L.oracle_q.argtypes = [C.c_void_p]
-            L.oracle_lattice.argtypes = [C.c_void_p, P(C.c_int32), d, P(C.c_int32)]
-            L.oracle_cells.argtypes = [C.c_void_p, P(C.c_int64)]
-            L.oracle_get_state.argtypes = [C.c_void_p, d, d]
-            L.oracle_set_state.argtypes = [C.c_void_p, d, d, C.c_int64]
-            L.oracle_collide_cell.argtypes = [C.c_void_p, C.c_int64, d, C.c_double, d, d]
-            L.oracle_apply_boundaries.argtypes = [C.c_void_p, C.c_int64]
-            L.oracle_lattice_params.argtypes = [C.c_void_p, d]
-            L.oracle_num_threads.restype = C.c_int32
-            L.oracle_set_anisotropy.restype = C.c_int32
-            L.oracle_set_anisotropy.argtypes = [C.c_void_p, d, d]
-            _lib = L
+            _lib = load_library(build())
     return _lib
 
 
@@ -133,10 +143,12 @@ class Oracle:
     """FP64 reference simulation of one Problem.  ``shape_tensor``: optional
     (6, nz, ny, nx) symmetric positive definite tensor S per cell (xx yy zz xy
     xz yz) for the anisotropic permeability K = k(phi) S^{-1} of the velocity
-    solve's fixed-point iteration (Sec. 3 remark)."""
+    solve's fixed-point iteration (Sec. 3 remark).  ``library``: a handle from
+    :func:`load_library` to run another build of the oracle source (the
+    pin tests run copies with a planted mistake through it)."""
 
-    def __init__(self, prob, phi=None, shape_tensor=None):
-        self.L = lib()
+    def __init__(self, prob, phi=None, shape_tensor=None, library=None):
+        self.L = lib() if library is None else library
         self.prob = prob
         self.params = params_from_problem(prob)
         self.flags = np.ascontiguousarray(prob.flags, dtype=np.uint8)
