@@ -34,6 +34,7 @@ WORKLOAD = dict(name="aneurysm384", n=384, q=27, lbm_steps=1000, seed=0)
 METRIC = "fluid MLUPS and % of HBM roofline, FP32 vs FP16-stored at stated error"
 UNIT = "MLUPS"
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 8000.0  # the ~8 TB/s the workload states as the HBM roofline
 
 
 def bytes_per_update(q, storage):
@@ -246,6 +247,7 @@ def run_ours(args):
         b2 = bytes_per_update(WORKLOAD["q"], st)
         variants[st] = {"value": nf * L / tv_mean / 1e6, "unit": UNIT,
                         "roofline_frac": b2 * nf / (tv_mean / L) / 1e9 / peak,
+                        "roofline_frac_nominal": b2 * nf / (tv_mean / L) / 1e9 / NOMINAL_HBM_GBS,
                         "bytes_per_update": b2, "traffic": load_traffic(name, st)}
         s2.close()
 
@@ -295,7 +297,8 @@ def run_ours(args):
                    "l2": f"{bpu * nf / 1e6:.0f} MB touched per time step and a 256 MB L2 flush "
                          "before each timed step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
+                     "frac": achieved / peak, "frac_nominal": achieved / NOMINAL_HBM_GBS,
+                     "nominal_peak": NOMINAL_HBM_GBS, "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "bytes_per_update": bpu,
                      "kernel": f"lbm_kernel<27,{st0},step> average over back-to-back launches"},
@@ -308,13 +311,17 @@ def run_ours(args):
         line["wall_shear"] = wall_shear_pass(torch, lbm, sim, prob, stream)
     if rank == 0 and not args.no_aniso:
         line["anisotropic"] = aniso_cost(torch, lbm, prob, args, flush, mlups / ws)
+    if rank == 0 and not args.no_config2:
+        line["config2"] = config2_throughput(torch, lbm, args, flush)
     if rank == 0 and not args.no_adjoint:
-        line["adjoint"] = adjoint_cost(torch, lbm, args)
+        line["adjoint"] = adjoint_cost(torch, lbm, args, args.adjoint_n)
+        if args.adjoint_n2 > 0:
+            line["adjoint_large"] = adjoint_cost(torch, lbm, args, args.adjoint_n2)
     if rank == 0 and not args.no_coil:
         line["coil"] = coil_study(torch, lbm, args)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(prob, sim_factory=lambda st: lbm.Simulation(prob, storage=st),
-                                            sample_steps=args.cpu_sample_steps)
+                                            sample_steps=args.cpu_sample_steps, error_steps=args.error_steps)
     sim.close()
     if rank == 0:
         print(json.dumps(line))
@@ -328,17 +335,20 @@ ADJOINT = dict(name="aneurysm128", n=128, q=27, T=500, K=50, seed=0)
 # S(t-1), lambda(t) read, lambda(t-1) write (3 x 108), omega 4, mu read + write
 # 8, phi 4, mask 4, rho - 1 gather 4, dJ/dphi read-modify-write 16.
 ADJOINT_BYTES_PER_UPDATE = 364
+L2_BYTES = 129e6  # GB300 L2 cache
 
 
-def adjoint_cost(torch, lbm, args):
+def adjoint_cost(torch, lbm, args, n):
     """Cost of lbm_adjoint (forward with checkpoints, segment replays, reverse
-    sweep) on the 128^3 aneurysm, T = 500 steps, checkpoint every K = 50 steps,
+    sweep) on the n^3 aneurysm, T = 500 steps, checkpoint every K = 50 steps,
     against T forward steps of the same problem; both timed with CUDA events on
     the launching stream.  A second figure keeps the whole trajectory (K = T,
-    no replay) when the device has room for it."""
+    no replay) when the device has room for it; from it, the reverse step
+    alone.  Its HBM fraction is reported only where the reverse step's bytes
+    exceed the L2 cache (at 128^3 its working set stays in L2)."""
     from lbm_inputs import aneurysm_problem
 
-    prob = aneurysm_problem(args.adjoint_n, q=ADJOINT["q"], seed=ADJOINT["seed"])
+    prob = aneurysm_problem(n, q=ADJOINT["q"], seed=ADJOINT["seed"])
     T, K = args.adjoint_T, args.adjoint_K
     sim = lbm.Simulation(prob)
     stream = torch.cuda.current_stream()
@@ -361,7 +371,7 @@ def adjoint_cost(torch, lbm, args):
     t_fwd, _ = timed(lambda: sim.step(T), 3)
     reg = np.ascontiguousarray(prob.region, dtype=np.uint8)
     grad = torch.empty(prob.flags.shape, dtype=torch.float64, device="cuda")
-    res = {"workload": f"aneurysm{args.adjoint_n} D3Q27 FP32, {prob.n_fluid} fluid cells, J = time-and-sac mean of "
+    res = {"workload": f"aneurysm{n} D3Q27 FP32, {prob.n_fluid} fluid cells, J = time-and-sac mean of "
                        f"rho|u|^2/2 over steps 1..{T}, gradient w.r.t. porosity",
            "T": T, "forward_s": t_fwd, "forward_step_us": 1e6 * t_fwd / T}
     variants = [("checkpointed", K)] + ([] if args.no_full_history else [("full_history", T)])
@@ -384,7 +394,9 @@ def adjoint_cost(torch, lbm, args):
             bytes_rev = ADJOINT_BYTES_PER_UPDATE * prob.n_fluid
             res[name].update({"reverse_step_us": 1e6 * t_rev, "reverse_vs_forward_step": t_rev / (t_fwd / T),
                               "reverse_bytes_per_update": ADJOINT_BYTES_PER_UPDATE,
-                              "reverse_roofline_frac": bytes_rev / t_rev / 1e9 / peak})
+                              "reverse_bytes_per_step": bytes_rev})
+            if bytes_rev > L2_BYTES:
+                res[name]["reverse_roofline_frac"] = bytes_rev / t_rev / 1e9 / peak
         del ws
     sim.close()
     return res
@@ -571,13 +583,20 @@ def coil_study(torch, lbm, args):
     return res
 
 
-def cpu_baseline(prob, sim_factory=None, sample_steps=40):
+def cpu_baseline(prob, sim_factory=None, sample_steps=30, error_steps=1000):
     """The FP64 oracle timed on the host cores on a bounded sample (the first
-    sample_steps time steps of the same workload).  When a GPU factory is given,
-    the GPU state after the same steps is compared with it for each storage."""
+    sample_steps time steps of the same workload).  When a GPU factory is
+    given, the same oracle run continues to error_steps and every storage
+    type is compared with it after the same number of steps: the largest
+    velocity and shear-rate deviation over the fluid cells relative to the
+    oracle's largest value, the relative L2 velocity deviation, and the mass
+    drift (M(T) - M(0)) / M(0) of the GPU run beside the oracle's (the porosity
+    term of Sec. 3 and the open boundaries make the mass change; both sides
+    must change it alike)."""
     from oracle.oracle import Oracle, num_threads
 
     o = Oracle(prob)
+    m0_ref = o.diag()[0]
     t0 = time.perf_counter()
     o.step(sample_steps)
     dt = time.perf_counter() - t0
@@ -585,21 +604,50 @@ def cpu_baseline(prob, sim_factory=None, sample_steps=40):
            "kind": "oracle",
            "sample": f"first {sample_steps} time steps of {WORKLOAD['name']} (D3Q27), FP64, OpenMP"}
     if sim_factory is not None:
+        steps = max(error_steps, sample_steps)
+        o.step(steps - sample_steps)
         r = o.moments()
+        drift_ref = (o.diag()[0] - m0_ref) / m0_ref
+        o.close()
         fl = prob.flags > 0
+        den = np.abs(r["u"][:, fl]).max()
+        gd = np.abs(r["gdot"][fl]).max()
+        l2 = np.sqrt((r["u"][:, fl] ** 2).sum())
         errs = {}
         for st in ("f32", "f16dev", "bf16dev"):
             s = sim_factory(st)
-            s.step(sample_steps)
+            m0 = s.diag()[0]
+            s.step(steps)
+            drift = (s.diag()[0] - m0) / m0
             g = s.moments()
-            den = np.abs(r["u"][:, fl]).max()
-            gd = np.abs(r["gdot"][fl]).max()
             errs[st] = {"u_max_rel": float(np.abs(g["u"][:, fl] - r["u"][:, fl]).max() / den),
+                        "u_l2_rel": float(np.sqrt(((g["u"][:, fl] - r["u"][:, fl]) ** 2).sum()) / l2),
                         "gdot_max_rel": float(np.abs(g["gdot"][fl] - r["gdot"][fl]).max() / gd),
-                        "after_steps": sample_steps}
+                        "mass_drift": float(drift), "mass_drift_oracle": float(drift_ref),
+                        "after_steps": steps}
             s.close()
         out["error_vs_oracle"] = errs
     return out
+
+
+def config2_throughput(torch, lbm, args, flush):
+    """The 256^3 aneurysm (FP32, D3Q27) over its 2000 time steps as one timed
+    run after a warm-up run, L2 flushed before each (CUDA events on the
+    launching stream)."""
+    from lbm_inputs import aneurysm_problem
+
+    prob = aneurysm_problem(256, q=27, seed=0)
+    L = 2000
+    sim, tv = time_variant(torch, lbm, prob, "f32", 2, 1, L, flush)
+    finite = bool(sim.diag()[7] == 0)
+    sim.close()
+    t = min(tv)
+    peak, _ = load_peaks()
+    bpu = bytes_per_update(27, "f32")
+    return {"workload": f"aneurysm256 D3Q27 f32-stored, {L} time steps, {prob.n_fluid} fluid cells",
+            "value": prob.n_fluid * L / t / 1e6, "unit": UNIT, "seconds": t,
+            "roofline_frac": bpu * prob.n_fluid * L / t / 1e9 / peak,
+            "roofline_frac_nominal": bpu * prob.n_fluid * L / t / 1e9 / NOMINAL_HBM_GBS, "finite": finite}
 
 
 def run_reference(args):
@@ -625,7 +673,10 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{WORKLOAD['name']} D3Q27, each step a bounded sample of {per} time steps",
-                       "box": [WORKLOAD["n"]] * 3, "fluid_cells": nf, "q": WORKLOAD["q"]},
+                       "box": [WORKLOAD["n"]] * 3, "fluid_cells": nf, "q": WORKLOAD["q"],
+                       "time_steps_per_step": per,
+                       "note": f"the oracle advances {per} time steps per bench step where the GPU arm advances "
+                               f"{WORKLOAD['lbm_steps']}; both report fluid-cell updates per second"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": num_threads(), "kind": "oracle",
                              "sample": f"{per} time steps per step of {WORKLOAD['name']}"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -640,6 +691,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--lbm-steps", type=int, default=WORKLOAD["lbm_steps"])
     ap.add_argument("--cpu-sample-steps", type=int, default=30)
+    ap.add_argument("--error-steps", type=int, default=WORKLOAD["lbm_steps"],
+                    help="time steps after which every storage type is compared with the oracle")
+    ap.add_argument("--no-config2", action="store_true", help="skip the 256^3, 2000-step throughput")
+    ap.add_argument("--adjoint-n2", type=int, default=256, help="second adjoint box (0: none)")
     ap.add_argument("--ref-sample-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

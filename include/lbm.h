@@ -169,14 +169,18 @@ lbm_status lbm_wall_shear(lbm_ctx* ctx, float* wss, int32_t dst_on_device);
  * device memory where they need the diagnostics, e.g. a monitoring thread of a
  * host application whose device allocator is owned by another framework.
  *  - Limit: at most 8,388,608 slots of the packed layout (lbm_list_length)
- *    and 1,048,576 cells on periodic faces, inlet or outlet (LBM_EINVAL
- *    beyond, use lbm_diag);
+ *    and a diagnostics launch of at most 98,305 blocks, which holds any
+ *    context with up to 1,048,576 cells on periodic faces, inlet or outlet
+ *    (LBM_EINVAL beyond, with the block count in the message; use lbm_diag);
  *    the array costs every GPU that loads the library 6.75 MiB until exit.
- *  - region: device memory or NULL (host regions are rejected with LBM_EINVAL,
- *    since copying them would need scratch); out: host memory; synchronises.
- *  - The context's device must be current.  The first call on a device looks
- *    up the array's device address (cudaGetSymbolAddress); make that first
- *    call before any stream capture begins.
+ *  - region: device memory of the current device, or NULL (host regions are
+ *    rejected with LBM_EINVAL, since copying them would need scratch; so is
+ *    device memory of another GPU); out: host memory; synchronises.
+ *  - The context's device must be current (its workspace may also be managed
+ *    memory).  Every call outside stream capture looks up the array's device
+ *    address (cudaGetSymbolAddress), so a device reset followed by a new
+ *    context is safe; a call during capture reuses the last address looked up
+ *    on that device, so make the first call on a device before any capture.
  *  - All calls share the array: calls that overlap on the GPU race; serialise
  *    them.  No state carries over from one call to the next. */
 lbm_status lbm_diag_noalloc(lbm_ctx* ctx, const uint8_t* region, double out[8]);
@@ -207,8 +211,10 @@ lbm_status lbm_diag_noalloc(lbm_ctx* ctx, const uint8_t* region, double out[8]);
  * or not positive definite at a cell with phi < 1; LBM_ENOMEM when the buffer
  * is too small.  lbm_adjoint differentiates the anisotropic solve too (the
  * implicit-function reverse of its converged velocity, with the porosity
- * dependence of the closure; S itself is held fixed).  Synchronises the
- * stream. */
+ * dependence of the closure; S itself is held fixed): its gradient is that of
+ * the converged solve, so give max_iter and tol that converge (the defaults
+ * do); with a truncated iteration the gradient no longer belongs to the
+ * computed objective.  Synchronises the stream. */
 size_t lbm_anisotropy_buffer_size(const lbm_ctx* ctx);
 lbm_status lbm_set_anisotropy(lbm_ctx* ctx, const float* shape, void* buffer, size_t bytes, int32_t max_iter,
                               float tol);

@@ -290,14 +290,6 @@ class TorchLBM:
             for i in idx_u:
                 j = int(self.opp[i])
                 new[i] = f[j] + feq[i] - feq[j]
-            for tng in range(3):
-                if tng == ax:
-                    continue
-                ct = torch.tensor(self.c[:, tng], dtype=torch.float64).view(-1, 1, 1, 1)
-                nres = ((new - feq) * ct)[cn == 0].sum(0)
-                cnt = float((self.c[unk.numpy(), tng] ** 2).sum())
-                for i in idx_u:
-                    new[i] = new[i] - float(self.c[i, tng]) * nres / cnt
             is_in = self.flags == INLET
             f = torch.where(is_in.unsqueeze(0) & unk.view(-1, 1, 1, 1), new, f)
         if b["outlet_axis"] >= 0 and bool((self.flags == OUTLET).any()):

@@ -235,8 +235,7 @@ __device__ __forceinline__ float macro_adjoint_aniso(const Params& P, int p, flo
 // boundary condition in, adjoints of the pulled populations out; the unknown
 // slots end at zero).  The condition is affine in the pulled populations and
 // in phi of the inlet cell: with P = phi rho = (g0 + 2 gm + phi) / (1 - ub.n),
-// unknown g_i = g_opp + 6 w_i P (c_i.ub) minus the tangential corrections
-// c_i,t N_t / n_t, N_t = sum_{c.n=0} (g_k - w_k (P - phi + P pe_k)) c_k,t.
+// unknown g_i = g_opp + 6 w_i P (c_i.ub).
 template <int Q>
 __device__ __forceinline__ void zou_he_adjoint(const Params& P, float prof, volatile float* park, float& phib)
 {
@@ -248,34 +247,8 @@ __device__ __forceinline__ void zou_he_adjoint(const Params& P, float prof, vola
     const float uby = -0.5f * P.gy + (ax == 1 ? sgn * un : 0.0f);
     const float ubz = -0.5f * P.gz + (ax == 2 ? sgn * un : 0.0f);
     const float ubn = (ax == 0 ? ubx : ax == 1 ? uby : ubz) * sgn;
-    const float uu = ubx * ubx + uby * uby + ubz * ubz;
     const float inv = 1.0f / (1.0f - ubn);
     float Pb = 0.0f;
-#pragma unroll
-    for (int tg = 0; tg < 3; ++tg) {
-        if (tg == ax) continue;
-        float ncnt = 0.0f, nb = 0.0f;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (c_axis<Q>(i, ax) * sgn > 0) {
-                const int ct = c_axis<Q>(i, tg);
-                ncnt += (float)(ct * ct);
-                if (ct) nb -= ct * park[i * kBlock];
-            }
-        }
-        nb /= ncnt;
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            const int ct = c_axis<Q>(k, tg);
-            if (c_axis<Q>(k, ax) * sgn == 0 && ct != 0) {
-                const float cu = cdot(L::cx(k), L::cy(k), L::cz(k), ubx, uby, ubz);
-                const float pe = 3.0f * cu + 4.5f * cu * cu - 1.5f * uu;
-                park[k * kBlock] += nb * ct;
-                Pb -= nb * L::w(k) * (1.0f + pe) * ct;
-                phib += nb * L::w(k) * ct;
-            }
-        }
-    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (c_axis<Q>(i, ax) * sgn > 0) {

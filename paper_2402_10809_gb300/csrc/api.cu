@@ -963,10 +963,11 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, int32_t obje
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds kNoAllocBytes for it until the process exits.  Its device
-// address is looked up once per device with cudaGetSymbolAddress (the name in
-// host code is only a host-side stand-in and must never be handed to a kernel).
-// The first lbm_diag_noalloc call on a device performs that lookup, so make
-// that first call before any stream capture begins.  All calls share the one
+// address is looked up with cudaGetSymbolAddress on every call made outside
+// stream capture (the name in host code is only a host-side stand-in and must
+// never be handed to a kernel); calls during a capture reuse the address of
+// the last uncaptured call on the device, so make the first call on a device
+// before any stream capture begins.  All calls share the one
 // array: calls that overlap on the GPU (other streams, other threads) race and
 // must be serialised by the caller.  Every slot a call reads is written earlier
 // in the same call, so leftover contents of a previous call do no harm.
@@ -986,15 +987,24 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocSlots];
 std::mutex g_noalloc_mutex;
 double* g_noalloc_ptr[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device (set-up, once per device).
-cudaError_t noalloc_scratch(int dev, double** out)
+// Device address of g_noalloc_scratch on the current device.  Looked up on
+// every call whose stream is not capturing (the module may be reloaded at
+// another address after a device reset); a capturing stream reuses the address
+// of the last uncaptured call on this device, so the first call on a device
+// must come before any capture.
+cudaError_t noalloc_scratch(int dev, cudaStream_t s, double** out)
 {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_noalloc_ptr[dev] = static_cast<double*>(p);
+    } else if (!g_noalloc_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_noalloc_ptr[dev];
     return cudaSuccess;
@@ -1014,24 +1024,31 @@ extern "C" lbm_status lbm_diag_noalloc(lbm_ctx* c, const uint8_t* region, double
     LBM_CUDA(cudaPointerGetAttributes(&attr, c->ws), "workspace attributes");
     int dev = -1;
     LBM_CUDA(cudaGetDevice(&dev), "current device");
-    if (attr.type != cudaMemoryTypeDevice || attr.device != dev)
-        return fail(c, LBM_EINVAL, "make the context's device current before lbm_diag_noalloc");
     if (dev < 0 || dev >= kMaxDevices) return fail(c, LBM_EINVAL, "device ordinal out of range");
+    if (attr.type == cudaMemoryTypeDevice && attr.device != dev)
+        return fail(c, LBM_EINVAL, "make the context's device current before lbm_diag_noalloc");
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return fail(c, LBM_EINVAL, "the context's workspace is not device or managed memory");
     if (region) {
         cudaPointerAttributes ra{};
         LBM_CUDA(cudaPointerGetAttributes(&ra, region), "region attributes");
         if (ra.type != cudaMemoryTypeDevice && ra.type != cudaMemoryTypeManaged)
             return fail(c, LBM_EINVAL, "lbm_diag_noalloc needs the region in device memory (or NULL)");
+        if (ra.type == cudaMemoryTypeDevice && ra.device != dev)
+            return fail(c, LBM_EINVAL, "the region lies on another device than the current one");
     }
     if (c->n_store == 0) {
         for (int k = 0; k < 8; ++k) out[k] = 0.0;
         return LBM_OK;
     }
     if (total_blocks(c->base) > kNoAllocMaxBlocks + 1)
-        return fail(c, LBM_EINVAL, "lbm_diag_noalloc handles at most " + std::to_string(32768 * 32) +
-                                       " general-path cells; use lbm_diag");
+        return fail(c, LBM_EINVAL, "lbm_diag_noalloc handles launches of at most " +
+                                       std::to_string(kNoAllocMaxBlocks + 1) + " blocks, this context needs " +
+                                       std::to_string(total_blocks(c->base)) + " (" +
+                                       std::to_string(c->base.n_general) + " general-path cells, " +
+                                       std::to_string(c->base.gen_block) + " per block); use lbm_diag");
     double* scratch = nullptr;
-    LBM_CUDA(noalloc_scratch(dev, &scratch), "cudaGetSymbolAddress of the diagnostics scratch");
+    LBM_CUDA(noalloc_scratch(dev, c->stream, &scratch), "address of the diagnostics scratch");
     double* partials = scratch;
     double* result = scratch + (size_t)(kNoAllocMaxBlocks + 1) * kDiagSlots;
     Params P = c->base;

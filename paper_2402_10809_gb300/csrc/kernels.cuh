@@ -154,6 +154,30 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Loads issued in program order (inline PTX, so that the compiler neither
+// sinks them to their first use nor places them behind a branch): a lean
+// cell requests all its per-slot words before its first dependent load, so
+// it waits for one memory latency before the row record instead of one per
+// word.
+__device__ __forceinline__ uint32_t ld_early_u32(const uint32_t* a)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(a));
+    return v;
+}
+__device__ __forceinline__ float ld_early_nc(const float* a)
+{
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(a));
+    return v;
+}
+__device__ __forceinline__ float ld_early(const float* a)
+{
+    float v;
+    asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(a));
+    return v;
+}
+
 // c . v for a lattice vector c with components in {-1, 0, 1}: only the needed
 // additions and sign flips (after unrolling every branch is decided at compile
 // time; IEEE arithmetic would not let the compiler drop 0 * v or v + 0).
@@ -459,8 +483,9 @@ __device__ __forceinline__ double inflow_mean(const Params& P, long long t)
 // Zou-He velocity inlet (Sec. 4) in non-equilibrium bounce-back form, in
 // deviation variables (phi = 1 on inlet cells).  With ub = u_in - g/2 and the
 // inward normal n: rho = (sum_{c.n=0} f + 2 sum_{c.n<0} f) / (1 - ub.n);
-// unknown f_i (c_i.n > 0) = f_opp + f_i^eq - f_opp^eq; then the tangential
-// residual N_t = sum_{c.n=0} (f - f^eq) c_t is removed so sum f c = rho ub.
+// unknown f_i (c_i.n > 0) = f_opp + f_i^eq - f_opp^eq, so that sum f = rho and
+// sum f c.n = rho ub.n.  No tangential correction: in D3Q27 it makes the
+// inlet unstable at the low relaxation times of the Carreau-Yasuda law.
 template <int Q>
 __device__ __forceinline__ void zou_he(const Params& P, float prof, float* g)
 {
@@ -481,33 +506,12 @@ __device__ __forceinline__ void zou_he(const Params& P, float prof, float* g)
     }
     const float drho = (g0 + 2.0f * gm + ubn) / (1.0f - ubn);
     const float rho = 1.0f + drho;
-    const float uu = ubx * ubx + uby * uby + ubz * ubz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (c_axis<Q>(i, ax) * sgn > 0) {
             const float cu = cdot(L::cx(i), L::cy(i), L::cz(i), ubx, uby, ubz);
             g[i] = g[opp(i)] + 6.0f * L::w(i) * rho * cu;
         }
-    }
-#pragma unroll
-    for (int tg = 0; tg < 3; ++tg) {
-        if (tg == ax) continue;
-        float nres = 0.0f, ncnt = 0.0f;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int cn = c_axis<Q>(i, ax) * sgn;
-            const int ct = c_axis<Q>(i, tg);
-            if (cn == 0 && ct != 0) {
-                const float cu = cdot(L::cx(i), L::cy(i), L::cz(i), ubx, uby, ubz);
-                const float geq = L::w(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
-                nres += (g[i] - geq) * ct;
-            }
-            if (cn > 0) ncnt += ct * ct;
-        }
-        const float corr = nres / ncnt;
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-            if (c_axis<Q>(i, ax) * sgn > 0) g[i] -= c_axis<Q>(i, tg) * corr;
     }
 }
 
@@ -588,11 +592,14 @@ __device__ __forceinline__ void block_reduce_diag(double* v, double* partials)
 // collision, store).  kModeMoments: pull + boundaries + moments and fields of
 // the current time.  kModeDiag: the same fields reduced to diagnostics.
 // park: this thread's column of a Q x kBlock shared array (time step only).
+// Lean cells (fast) get their row id, porosity and omega(t-1) from the caller,
+// which loads them together with the mask; general cells load their own.
 template <int Q, class T, int MODE, bool fast, bool AN>
-__device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t mask, double* dv, volatile float* park)
+__device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t mask, double* dv, volatile float* park,
+                                          uint32_t row_pre = 0, float phi_pre = 0.0f, float om_pre = 0.0f)
 {
     using L = Lattice<Q>;
-    const float phi = __ldg(P.phi + p);
+    const float phi = fast ? phi_pre : __ldg(P.phi + p);
     const T* __restrict__ fs = static_cast<const T*>(P.fsrc);
     const uint32_t n = (uint32_t)P.n_store;
     float g[Q];
@@ -603,7 +610,7 @@ __device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t mask,
     if (fast) {
         // y - c_i never wraps here and every offset fits 32 bits (the host
         // sends larger layouts down the general path).
-        row = P.rows[p];
+        row = row_pre;
         rb = row_bases(P, row);
         x = p - rb.b[4];
 #pragma unroll
@@ -646,7 +653,7 @@ __device__ __forceinline__ void cell_impl(const Params& P, int p, uint32_t mask,
     const float pyz = fmaf(M.uy, fmaf(-M.sigma, M.uz, 0.5f * M.Fz), fmaf(0.5f * M.Fy, M.uz, m.syz));
     const float pn2 = fmaf(pxx, pxx, fmaf(pyy, pyy, fmaf(pzz, pzz, 2.0f * fmaf(pxy, pxy, fmaf(pxz, pxz, pyz * pyz)))));
     // semi-explicit shear rate gdot(t) = omega(t-1) ||Pi||_F / (c_s^2 rho)
-    const float om_prev = P.omega[p];
+    const float om_prev = fast ? om_pre : P.omega[p];
     const float gdot = __fdividef(3.0f * om_prev * sqrtf(pn2), M.rho);
     const float om = relaxation_rate(P, M.rho, gdot);
 
@@ -756,12 +763,13 @@ __device__ __forceinline__ void ghost_slot(const Params& P, int p, uint32_t mask
 // Lean-path thread of slot p: ghost slots store zeros where needed, general
 // cells are left to the general blocks.
 template <int Q, class T, int MODE, bool AN>
-__device__ __forceinline__ void lean_body(const Params& P, int p, uint32_t mask, double* dv, volatile float* park)
+__device__ __forceinline__ void lean_body(const Params& P, int p, uint32_t mask, double* dv, volatile float* park,
+                                          uint32_t row, float phi, float om)
 {
     if (mask & kGhostBit)
         ghost_slot<Q, T, MODE>(P, p, mask);
     else if (!(mask & kGeneralBits) && !P.wide)
-        cell_impl<Q, T, MODE, true, AN>(P, p, mask, dv, park);
+        cell_impl<Q, T, MODE, true, AN>(P, p, mask, dv, park, row, phi, om);
 }
 
 // Shared column for parking the pulled populations during a time step.
@@ -793,7 +801,15 @@ __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS) lbm_kernel(const Param
         }
     } else {
         const int p = ((int)blockIdx.x - nbg) * kBlock + (int)threadIdx.x;
-        if (p < P.n_store) lean_body<Q, T, MODE, AN>(P, p, P.mask[p], dv, park);
+        if (p < P.n_store) {
+            // all per-slot words of the cell at once (ghost and general
+            // slots load them too, harmlessly: every slot has all four)
+            const uint32_t mask = ld_early_u32(P.mask + p);
+            const uint32_t row = ld_early_u32(P.rows + p);
+            const float phi = ld_early_nc(P.phi + p);
+            const float om = ld_early(P.omega + p);
+            lean_body<Q, T, MODE, AN>(P, p, mask, dv, park, row, phi, om);
+        }
     }
     if (MODE == kModeDiag) block_reduce_diag(dv, P.partials);
 }

@@ -201,7 +201,7 @@ def test_wall_shear_objective_independent_of_checkpoint_interval(lbm):
     assert J0 == J1 and np.array_equal(g0.cpu().numpy(), g1.cpu().numpy())
 
 
-@pytest.mark.parametrize("objective", ["ke"])
+@pytest.mark.parametrize("objective", ["ke", "wss"])
 def test_anisotropic_permeability_matches_reference_gradient(lbm, objective):
     """The adjoint through the fixed-point velocity solve of an anisotropic
     permeability (lbm_set_anisotropy): implicit-function reverse of the

@@ -62,10 +62,13 @@ def test_c_and_torch_oracles_agree_periodic_random_porosity():
 
 @pytest.mark.parametrize("q", [19, 27])
 def test_zou_he_momentum_identity(q):
-    """After the inlet reconstruction every inlet cell carries
-    sum_i f_i c_i = rho (u_in - g/2), rho = sum_i f_i (phi = 1), with the
-    Hagen-Poiseuille profile u_in = 2 v(t) (1 - r^2/R^2) n (Sec. 4), from
-    arbitrary (perturbed) incoming populations."""
+    """After the inlet reconstruction (non-equilibrium bounce-back of the
+    unknown populations, Sec. 4) every inlet cell carries rho = sum_i f_i (phi
+    = 1), the normal momentum rho u_in.n of the Hagen-Poiseuille profile
+    u_in = 2 v(t) (1 - r^2/R^2) n exactly, and the tangential momentum
+    rho ub_t + N_t with N_t = sum_{c.n=0} (f - f^eq(rho, ub)) c_t, the residual
+    of the populations that stream along the inlet plane (no tangential
+    correction), from arbitrary (perturbed) incoming populations."""
     prob = aneurysm_problem(24, q=q, small=True, u0=0.04, amp=0.5, period=30.0)
     o = Oracle(prob)
     rng = np.random.default_rng(q)
@@ -80,17 +83,25 @@ def test_zou_he_momentum_identity(q):
     b = prob.bc
     v = b["u0"] * (1 + b["amp"] * math.sin(2 * math.pi * t / b["period"]))
     n_in = 0
+    largest_residual = 0.0
+    inplane = c[:, 2] == 0
     for k, idx in enumerate(cells):
         if prob.flags.reshape(-1)[idx] != 2:
             continue
         n_in += 1
         x, y = idx % nx, (idx // nx) % ny
         r2 = (x + 0.5 - b["inlet_center"][0]) ** 2 + (y + 0.5 - b["inlet_center"][1]) ** 2
-        un = 2 * v * max(0.0, 1 - r2 / b["inlet_radius"] ** 2)
+        ub = np.array([0.0, 0.0, 2 * v * max(0.0, 1 - r2 / b["inlet_radius"] ** 2)])
         rho = f[k].sum()
         mom = f[k] @ c
-        assert np.abs(mom - rho * np.array([0.0, 0.0, un])).max() < 1e-15
+        cu = c @ ub
+        feq = w * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * ub @ ub)
+        resid = ((f[k] - feq)[inplane, None] * c[inplane]).sum(0)
+        assert abs(mom[2] - rho * ub[2]) < 1e-15
+        assert np.abs(mom[:2] - resid[:2]).max() < 1e-15
+        largest_residual = max(largest_residual, np.abs(resid[:2]).max())
     assert n_in > 20
+    assert largest_residual > 1e-4  # the tangential residual is genuinely left in place
 
 
 def test_reference_gradient_matches_finite_differences():

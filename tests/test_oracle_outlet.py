@@ -93,7 +93,8 @@ def force_pins(u, rho, u_max):
 def pressure_pins(u, rho, u_max):
     """Density slope against -6 nu u_max / h^2 (relative), the outlet density
     against rho_out and the residual of the linear fit (both relative to the
-    density drop along the channel), and the spread across y."""
+    density drop along the channel), and the spread across y over the
+    downstream half (the inlet's developing region is not the outlet's)."""
     z = np.arange(NZ)
     r = rho[:, 1:-1].mean(axis=1)
     slope, icpt = np.polyfit(z[2:-2], r[2:-2], 1)
@@ -101,7 +102,7 @@ def pressure_pins(u, rho, u_max):
     drop = abs(expect) * (NZ - 1)
     fit = np.abs(r[2:-2] - (slope * z[2:-2] + icpt)).max() / drop
     out = np.abs(rho[NZ - 1, 1:-1] - 1.0).max() / drop
-    across = max(np.ptp(rho[k, 1:-1]) for k in range(1, NZ)) / drop
+    across = max(np.ptp(rho[k, 1:-1]) for k in range(NZ // 2, NZ)) / drop
     return abs(slope / expect - 1.0), out, fit, across
 
 
@@ -109,8 +110,8 @@ def pressure_pins(u, rho, u_max):
 def test_body_force_poiseuille_leaves_the_outlet_undisturbed(q):
     u, rho, u_max = run(q, "force")
     err, drho, flux = force_pins(u, rho, u_max)
-    assert err < 1e-7  # measured 3.3e-9
-    assert drho < 1e-10  # measured 1.0e-12
+    assert err < 1e-7  # measured 4.6e-9
+    assert drho < 1e-10  # measured 5.0e-12
     assert flux < 1e-10  # steady: the mass flux is the same through every slice
 
 
@@ -118,10 +119,10 @@ def test_body_force_poiseuille_leaves_the_outlet_undisturbed(q):
 def test_pressure_driven_channel_has_the_poiseuille_pressure_drop(q):
     u, rho, u_max = run(q, "pressure")
     slope, out, fit, across = pressure_pins(u, rho, u_max)
-    assert slope < 1e-4  # measured 1.6e-5 (weak compressibility)
+    assert slope < 1e-4  # measured 1.8e-5 (weak compressibility)
     assert out < 1e-4  # measured 1.0e-5 of the drop
-    assert fit < 1e-4  # measured 1.7e-6
-    assert across < 1e-4  # measured 1.6e-6
+    assert fit < 1e-4  # measured 2.8e-6
+    assert across < 1e-4  # measured 4.1e-6
     # the profile stays the parabola up to the compressibility of the scheme
     assert np.abs(u[NZ - 1, 1:-1] - parabola(u_max)[1:-1]).max() / u_max < 1e-4
 
