@@ -311,6 +311,8 @@ def run_ours(args):
         line["wall_shear"] = wall_shear_pass(torch, lbm, sim, prob, stream)
     if rank == 0 and not args.no_aniso:
         line["anisotropic"] = aniso_cost(torch, lbm, prob, args, flush, mlups / ws)
+    if rank == 0 and not args.no_slabs:
+        line["slabs_one_gpu"] = slab_overhead(torch, lbm, prob, args, flush, mlups / ws)
     if rank == 0 and not args.no_config2:
         line["config2"] = config2_throughput(torch, lbm, args, flush)
     if rank == 0 and not args.no_adjoint:
@@ -630,6 +632,36 @@ def cpu_baseline(prob, sim_factory=None, sample_steps=30, error_steps=1000):
     return out
 
 
+def slab_overhead(torch, lbm, prob, args, flush, unsharded):
+    """The headline workload split into z-slabs on this one GPU (the
+    decomposition a box too large for one GPU would use across GPUs): the
+    slabs' step kernels plus one face-exchange launch per face and time step;
+    CUDA events around args.lbm_steps time steps after a warm-up run."""
+    from paper_2402_10809_gb300 import slabs
+
+    res = {}
+    stream = torch.cuda.current_stream()
+    for ns in (2, 4):
+        sl = slabs.SlabSimulation(prob, ns, storage="f32")
+        sl.step(args.lbm_steps)
+        ts = []
+        for _ in range(3):
+            flush_l2(torch, flush)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sl.step(args.lbm_steps)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        finite = bool(sl.diag()[7] == 0)
+        sl.close()
+        v = prob.n_fluid * args.lbm_steps / min(ts) / 1e6
+        res[f"slabs{ns}"] = {"value": v, "unit": UNIT, "vs_unsharded": v / unsharded, "bounds": sl.bounds,
+                             "finite": finite}
+    return res
+
+
 def config2_throughput(torch, lbm, args, flush):
     """The 256^3 aneurysm (FP32, D3Q27) over its 2000 time steps as one timed
     run after a warm-up run, L2 flushed before each (CUDA events on the
@@ -694,6 +726,7 @@ def main():
     ap.add_argument("--error-steps", type=int, default=WORKLOAD["lbm_steps"],
                     help="time steps after which every storage type is compared with the oracle")
     ap.add_argument("--no-config2", action="store_true", help="skip the 256^3, 2000-step throughput")
+    ap.add_argument("--no-slabs", action="store_true", help="skip the z-slab split on one GPU")
     ap.add_argument("--adjoint-n2", type=int, default=256, help="second adjoint box (0: none)")
     ap.add_argument("--ref-sample-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")

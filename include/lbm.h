@@ -219,6 +219,57 @@ size_t lbm_anisotropy_buffer_size(const lbm_ctx* ctx);
 lbm_status lbm_set_anisotropy(lbm_ctx* ctx, const float* shape, void* buffer, size_t bytes, int32_t max_iter,
                               float tol);
 
+/* z-slab decomposition of one problem over several contexts (one per GPU, or
+ * several on one device): the partition the fused step admits (Sec. 3: a cell
+ * pulls only from its 26 neighbours, so a slab of z-planes needs one plane of
+ * its neighbours per face and, across a face, only the 9 (D3Q27) or 5 (D3Q19)
+ * populations whose c_z points into the slab).  The paper runs one GPU; this
+ * is the sharding of a box too large for one.  A slab owns z in [z0, z1) of
+ * the box and is set up with lbm_init on the sub-box [z0 - h0, z1 + h1) of the
+ * box's flags and porosity, h0 = 1 if it has a lower neighbour (z0 > 0), h1 = 1
+ * if it has an upper one, and the box's other parameters unchanged (the inlet
+ * and outlet stay where they are: only the slab that holds their cells sees
+ * them).  Boxes periodic in z are not sharded.
+ *
+ * lbm_slab_bounds: z0 of every slab and the box's nz in z_bounds[0..nslabs],
+ *   chosen so that the slabs hold about equal numbers of packed slots, every
+ *   slab at least one plane; host only (no device, no context).
+ * lbm_plane_slots: first slot and number of slots of z-plane z in the packed
+ *   layout of (grid, flags) (planes are contiguous ranges); host only.
+ * lbm_set_halo: marks the first lo_planes and last hi_planes (0 or 1 each)
+ *   z-planes of the context as halo planes: lbm_step neither updates them nor
+ *   do lbm_moments (zeros there) and lbm_diag count them; their populations
+ *   come from the neighbours (their slots become ghost slots without stores;
+ *   calling it again restores the previous halo planes first).  LBM_EINVAL
+ *   for other counts, for no interior plane left, or for a box periodic in z;
+ *   lbm_adjoint refuses a context with halo planes (the adjoint runs on one
+ *   domain).  Synchronises the stream.
+ * lbm_halo_message_size: bytes a face sends (side 0 the lower face, 1 the
+ *   upper face): the populations of the interior plane next to the face whose
+ *   c_z points through it, [directions in increasing index][plane slots] in
+ *   the storage type; 0 without a halo on that side.
+ * lbm_halo_pack / lbm_halo_unpack: device buffers of that layout; pack reads
+ *   the interior plane next to the face, unpack writes the halo plane of the
+ *   face (the message the neighbour packed on its side facing this one: side 1
+ *   of the lower slab pairs with side 0 of the upper slab).  Asynchronous on
+ *   the context's stream.
+ * lbm_halo_exchange: both copies of one face between two contexts on one
+ *   device in one launch (lower's top interior plane to upper's lower halo,
+ *   upper's first interior plane to lower's upper halo); the two contexts must
+ *   share one stream.  LBM_EINVAL when the face's planes do not match.
+ * One time step of the sharded problem: lbm_step(ctx, 1) on every slab, then
+ * every face exchanged (or packed, sent, received and unpacked).  Every cell's
+ * arithmetic is then the same as in the unsharded box, so the results are
+ * bit-identical to it; the diagnostics of the box are the sums (mass, kinetic
+ * energy, region sums, non-finite count) and extrema of the slabs'. */
+lbm_status lbm_slab_bounds(const lbm_grid* grid, const uint8_t* flags, int32_t nslabs, int32_t* z_bounds);
+lbm_status lbm_plane_slots(const lbm_grid* grid, const uint8_t* flags, int32_t z, int64_t* first, int64_t* count);
+lbm_status lbm_set_halo(lbm_ctx* ctx, int32_t lo_planes, int32_t hi_planes);
+size_t lbm_halo_message_size(const lbm_ctx* ctx, int32_t side);
+lbm_status lbm_halo_pack(lbm_ctx* ctx, int32_t side, void* dst);
+lbm_status lbm_halo_unpack(lbm_ctx* ctx, int32_t side, const void* src);
+lbm_status lbm_halo_exchange(lbm_ctx* lower, lbm_ctx* upper);
+
 /* Volume-averaged porosity of a voxelised coil, the input that lbm_init takes
  * as the porosity of the averaged simulations (Sec. 4: the porosity field is
  * the windowed convolution of the voxelised coil with a uniform averaging

@@ -348,15 +348,19 @@ __device__ __forceinline__ void outlet_adjoint(const AdjParams& A, const Coords&
 // its pull sources), all filled by asynchronous copies issued at the start so
 // that their latencies overlap; the per-cell scalars are loaded before any
 // wait for the same reason.
+// Lean cells (fast) get their row id, porosity, omega(t-1) and mu(t) from the
+// caller, which loads them together with the mask.
 template <int Q, class T, bool fast, bool AN>
 __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t mask, volatile float* park,
-                                             volatile float* lampark, volatile float* dpark, double& jv)
+                                             volatile float* lampark, volatile float* dpark, double& jv,
+                                             uint32_t row_pre = 0, float phi_pre = 0.0f, float om_pre = 0.0f,
+                                             float mu_pre = 0.0f)
 {
     using L = Lattice<Q>;
     const Params& P = A.F;
-    const float phi = __ldg(P.phi + p);
-    const float om_prev = P.omega[p];
-    const float bmu = A.first ? 0.0f : A.mu[p];
+    const float phi = fast ? phi_pre : __ldg(P.phi + p);
+    const float om_prev = fast ? om_pre : P.omega[p];
+    const float bmu = A.first ? 0.0f : (fast ? mu_pre : A.mu[p]);
     const double gphi0 = A.gphi[p];
     const bool porous = (mask & kPorousBit) != 0u;
     const T* __restrict__ fs = static_cast<const T*>(P.fsrc);
@@ -374,7 +378,7 @@ __device__ __forceinline__ void adjoint_cell(const AdjParams& A, int p, uint32_t
             for (int i = 0; i < Q; ++i) cp_async4(lampark + i * kBlock, A.lam_in + (size_t)i * n + p);
         }
         if (fast) {
-            row = P.rows[p];
+            row = row_pre;
             rb = row_bases(P, row);
             x = p - rb.b[4];
 #pragma unroll
@@ -702,10 +706,16 @@ __global__ void __launch_bounds__(kBlock, TPS / kBlock) adjoint_kernel(const Adj
     } else {
         const int p = ((int)blockIdx.x - nbg) * kBlock + (int)threadIdx.x;
         if (p < P.n_store) {
-            const uint32_t mask = P.mask[p];
+            // every per-slot word of the cell at once (one memory latency
+            // before the row record instead of one per word)
+            const uint32_t mask = ld_early_u32(P.mask + p);
+            const uint32_t row = ld_early_u32(P.rows + p);
+            const float phi = ld_early_nc(P.phi + p);
+            const float om = ld_early_nc(P.omega + p);
+            const float mu = A.first ? 0.0f : ld_early(A.mu + p);
             // ghost slots hold no state; general cells belong to the general blocks
             if (!(mask & (kGhostBit | kGeneralBits)) && !P.wide)
-                adjoint_cell<Q, T, true, AN>(A, p, mask, park, lampark, dpark, jv);
+                adjoint_cell<Q, T, true, AN>(A, p, mask, park, lampark, dpark, jv, row, phi, om, mu);
         }
     }
     if (A.objective) {

@@ -158,6 +158,10 @@ struct lbm_ctx {
     std::vector<long long> host_idx;  // dense index of each slot, -1 for ghost slots
     std::vector<uint32_t> out_slots;  // slots of the outlet cells
     std::vector<uint32_t> general;    // slots of the general-path cells
+    std::vector<long long> plane_first;  // [nz + 1] first slot of each z-plane (contiguous per plane)
+    int halo_lo = 0, halo_hi = 0;     // halo planes of a z-slab (lbm_set_halo)
+    std::vector<uint32_t> halo_masks;    // the masks the halo planes had before they became halos
+    std::vector<uint32_t> all_general;   // the general list without halo planes removed
     std::string err;
 
     template <class T>
@@ -284,6 +288,13 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
         total += ext[r];
     }
     c->n_store = (int)total;
+    c->plane_first.assign((size_t)nz + 1, 0);
+    for (int z = 0; z < nz; ++z) {
+        long long cnt = 0;
+        for (int y = 0; y < ny; ++y) cnt += ext[y + ny * z];
+        c->plane_first[z + 1] = c->plane_first[z] + cnt;
+    }
+    c->halo_lo = c->halo_hi = 0;
     c->L = layout(grid, c->n_store);
     if (workspace_bytes < c->L.end)
         return fail(c, LBM_ENOMEM, "workspace smaller than lbm_workspace_size(grid, " + std::to_string(c->n_store) +
@@ -385,6 +396,8 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
         if (wide || (hmask[p] & kGeneralBits)) c->general.push_back((uint32_t)p);
     }
     c->n_out = (int)c->out_slots.size();
+    c->all_general = c->general;
+    c->halo_masks.clear();
     if (!c->general.empty())
         LBM_CUDA(cudaMemcpyAsync(c->at<uint32_t>(c->L.general), c->general.data(), c->general.size() * 4,
                                  cudaMemcpyHostToDevice, c->stream), "copy general list");
@@ -802,6 +815,7 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, int32_t obje
     if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
     if (T < 1 || K < 1) return fail(c, LBM_EINVAL, "T and K must be >= 1");
     if (objective != 0 && objective != 1) return fail(c, LBM_EINVAL, "objective must be 0 (kinetic energy) or 1 (wall shear)");
+    if (c->halo_lo || c->halo_hi) return fail(c, LBM_EINVAL, "the adjoint runs on a whole box, not on a z-slab");
     if (!region || !workspace || !grad || !J) return fail(c, LBM_EINVAL, "null pointer argument");
     if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
         return fail(c, LBM_EINVAL, "adjoint workspace not 256-byte aligned");
@@ -948,6 +962,242 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, int32_t obje
     for (size_t b = 0; b < nparts; ++b) sum += hp[b];
     *J = sum;
     return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// z-slab decomposition: one context per slab of z-planes plus one halo plane on
+// each side that has a neighbour.  A step pulls across a slab face only the
+// directions with c_z pointing into the slab, from the neighbour's plane next
+// to the face; those populations are copied into the halo plane after every
+// step (directly on one device, or packed for a message between processes).
+// ---------------------------------------------------------------------------
+namespace {
+
+// Directions whose c_z equals cz, in increasing index order (the order of a
+// packed halo message).
+int dirs_with_cz(int q, int cz, int* out)
+{
+    int n = 0;
+    for (int i = 0; i < q; ++i) {
+        const int c = q == 19 ? Lattice<19>::cz(i) : Lattice<27>::cz(i);
+        if (c == cz) out[n++] = i;
+    }
+    return n;
+}
+
+// Slots of every z-plane of a box (host form of the packed layout).
+bool plane_counts(const lbm_grid* g, const uint8_t* flags, std::vector<long long>& cnt)
+{
+    std::vector<int> ext;
+    host_spans(g, flags, nullptr, &ext);
+    cnt.assign((size_t)g->nz, 0);
+    for (int z = 0; z < g->nz; ++z)
+        for (int y = 0; y < g->ny; ++y) cnt[z] += ext[(size_t)y + (size_t)g->ny * z];
+    return true;
+}
+
+// The plane a side of the face sends (interior) and the plane it receives
+// (halo), and the direction set of each.  side 0: the lower face, side 1: the
+// upper face.
+struct FaceSpec {
+    int send_plane, recv_plane, send_cz, recv_cz;
+};
+FaceSpec face_of(const lbm_ctx* c, int side)
+{
+    const int nz = c->grid.nz;
+    if (side == 0) return {c->halo_lo, 0, -1, +1};
+    return {nz - 1 - c->halo_hi, nz - 1, +1, -1};
+}
+
+size_t elem_of(const lbm_ctx* c) { return elem_size(c->grid.storage); }
+
+}  // namespace
+
+extern "C" lbm_status lbm_plane_slots(const lbm_grid* grid, const uint8_t* flags, int32_t z, int64_t* first,
+                                      int64_t* count)
+{
+    if (!grid_ok(grid) || !flags || !first || !count || z < 0 || z >= grid->nz) return LBM_EINVAL;
+    std::vector<long long> cnt;
+    plane_counts(grid, flags, cnt);
+    long long f = 0;
+    for (int k = 0; k < z; ++k) f += cnt[k];
+    *first = f;
+    *count = cnt[z];
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_slab_bounds(const lbm_grid* grid, const uint8_t* flags, int32_t nslabs, int32_t* z_bounds)
+{
+    if (!grid_ok(grid) || !flags || !z_bounds || nslabs < 1 || nslabs > grid->nz) return LBM_EINVAL;
+    std::vector<long long> cnt;
+    plane_counts(grid, flags, cnt);
+    long long total = 0;
+    for (long long v : cnt) total += v;
+    // boundary k at the first plane whose cumulative slot count reaches k/nslabs
+    // of the total, kept strictly increasing so that every slab owns a plane
+    z_bounds[0] = 0;
+    long long acc = 0;
+    int z = 0;
+    for (int k = 1; k < nslabs; ++k) {
+        const long long target = (total * k + nslabs / 2) / nslabs;
+        while (z < grid->nz && acc + cnt[z] <= target) acc += cnt[z++];
+        int b = z;
+        if (b <= z_bounds[k - 1]) b = z_bounds[k - 1] + 1;
+        if (b > grid->nz - (nslabs - k)) b = grid->nz - (nslabs - k);
+        while (z < b) acc += cnt[z++];
+        z_bounds[k] = b;
+    }
+    z_bounds[nslabs] = grid->nz;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_halo(lbm_ctx* c, int32_t lo_planes, int32_t hi_planes)
+{
+    if (!c) return LBM_EINVAL;
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    if (lo_planes < 0 || lo_planes > 1 || hi_planes < 0 || hi_planes > 1)
+        return fail(c, LBM_EINVAL, "halo planes: 0 or 1 on each side");
+    if (c->grid.nz - lo_planes - hi_planes < 1) return fail(c, LBM_EINVAL, "a slab needs an interior plane");
+    if ((lo_planes || hi_planes) && c->grid.periodic[2])
+        return fail(c, LBM_EINVAL, "halo planes need a box that is not periodic in z");
+    // Halo slots become ghost slots without zero stores: every kernel skips
+    // them, so the step neither updates them nor do moments and diagnostics
+    // count them, at no cost to the cells.  The previous halo planes get their
+    // masks back first.
+    const int nz = c->grid.nz;
+    uint32_t* mask = c->at<uint32_t>(c->L.mask);
+    auto ranges = [&](int lo, int hi, long long r[2][2]) {
+        r[0][0] = c->plane_first[0];
+        r[0][1] = c->plane_first[lo];
+        r[1][0] = c->plane_first[nz - hi];
+        r[1][1] = c->plane_first[nz];
+    };
+    long long old_r[2][2], new_r[2][2];
+    ranges(c->halo_lo, c->halo_hi, old_r);
+    size_t at = 0;
+    for (auto& r : old_r) {
+        const size_t cnt = (size_t)(r[1] - r[0]);
+        if (cnt)
+            LBM_CUDA(cudaMemcpyAsync(mask + r[0], c->halo_masks.data() + at, cnt * 4, cudaMemcpyHostToDevice,
+                                     c->stream), "restore halo masks");
+        at += cnt;
+    }
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "restore halo masks");
+    ranges(lo_planes, hi_planes, new_r);
+    c->halo_masks.assign((size_t)(new_r[0][1] - new_r[0][0] + new_r[1][1] - new_r[1][0]), 0u);
+    at = 0;
+    for (auto& r : new_r) {
+        const size_t cnt = (size_t)(r[1] - r[0]);
+        if (cnt) {
+            LBM_CUDA(cudaMemcpyAsync(c->halo_masks.data() + at, mask + r[0], cnt * 4, cudaMemcpyDeviceToHost,
+                                     c->stream), "save halo masks");
+            LBM_CUDA(launch_fill_u32(mask + r[0], (long long)cnt, kGhostBit, c->stream), "mark halo slots");
+        }
+        at += cnt;
+    }
+    c->general.clear();
+    for (uint32_t p : c->all_general)
+        if (!((long long)p < new_r[0][1] || (long long)p >= new_r[1][0])) c->general.push_back(p);
+    if (!c->general.empty())
+        LBM_CUDA(cudaMemcpyAsync(c->at<uint32_t>(c->L.general), c->general.data(), c->general.size() * 4,
+                                 cudaMemcpyHostToDevice, c->stream), "copy general list");
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "halo set-up sync");
+    c->base.n_general = (int)c->general.size();
+    c->halo_lo = lo_planes;
+    c->halo_hi = hi_planes;
+    return LBM_OK;
+}
+
+extern "C" size_t lbm_halo_message_size(const lbm_ctx* c, int32_t side)
+{
+    if (!c || !c->ready || (side != 0 && side != 1)) return 0;
+    if ((side == 0 && !c->halo_lo) || (side == 1 && !c->halo_hi)) return 0;
+    const FaceSpec f = face_of(c, side);
+    int d[27];
+    const int nd = dirs_with_cz(c->grid.q, f.send_cz, d);
+    return (size_t)nd * (size_t)(c->plane_first[f.send_plane + 1] - c->plane_first[f.send_plane]) * elem_of(c);
+}
+
+static lbm_status halo_pack_unpack(lbm_ctx* c, int side, void* dst, const void* src, bool pack)
+{
+    if (!c) return LBM_EINVAL;
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    if (side != 0 && side != 1) return fail(c, LBM_EINVAL, "side must be 0 (lower face) or 1 (upper face)");
+    if ((side == 0 && !c->halo_lo) || (side == 1 && !c->halo_hi))
+        return fail(c, LBM_EINVAL, "no halo plane on this side (lbm_set_halo)");
+    if (pack ? !dst : !src) return fail(c, LBM_EINVAL, "null buffer");
+    const FaceSpec f = face_of(c, side);
+    const int plane = pack ? f.send_plane : f.recv_plane;
+    int d[27];
+    const int nd = dirs_with_cz(c->grid.q, pack ? f.send_cz : f.recv_cz, d);
+    const long long first = c->plane_first[plane], count = c->plane_first[plane + 1] - first;
+    const size_t es = elem_of(c), n = (size_t)c->n_store;
+    char* state = static_cast<char*>(c->f(c->cur));
+    HaloCopy H{};
+    H.ntask = nd;
+    H.elem = (int)es;
+    for (int k = 0; k < nd; ++k) {
+        char* slot = state + ((size_t)d[k] * n + (size_t)first) * es;
+        H.count[k] = count;
+        if (pack) {
+            H.src[k] = slot;
+            H.dst[k] = static_cast<char*>(dst) + (size_t)k * count * es;
+        } else {
+            H.src[k] = static_cast<const char*>(src) + (size_t)k * count * es;
+            H.dst[k] = slot;
+        }
+    }
+    LBM_CUDA(launch_halo_copy(H, c->stream), pack ? "halo pack" : "halo unpack");
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_halo_pack(lbm_ctx* c, int32_t side, void* dst)
+{
+    return halo_pack_unpack(c, side, dst, nullptr, true);
+}
+
+extern "C" lbm_status lbm_halo_unpack(lbm_ctx* c, int32_t side, const void* src)
+{
+    return halo_pack_unpack(c, side, nullptr, src, false);
+}
+
+extern "C" lbm_status lbm_halo_exchange(lbm_ctx* lower, lbm_ctx* upper)
+{
+    if (!lower || !upper || lower == upper) return LBM_EINVAL;
+    if (!lower->ready || !upper->ready) return fail(lower, LBM_ESTATE, "context not initialised");
+    if (!lower->halo_hi || !upper->halo_lo)
+        return fail(lower, LBM_EINVAL, "the lower slab needs an upper halo plane and the upper slab a lower one");
+    if (lower->grid.q != upper->grid.q || lower->grid.storage != upper->grid.storage ||
+        lower->grid.nx != upper->grid.nx || lower->grid.ny != upper->grid.ny)
+        return fail(lower, LBM_EINVAL, "slabs of different lattices, storage types or x-y extents");
+    if (lower->stream != upper->stream) return fail(lower, LBM_EINVAL, "the two slabs must share one stream");
+    const FaceSpec fl = face_of(lower, 1), fu = face_of(upper, 0);
+    const long long a = lower->plane_first[fl.send_plane + 1] - lower->plane_first[fl.send_plane];
+    const long long b = upper->plane_first[fu.recv_plane + 1] - upper->plane_first[fu.recv_plane];
+    const long long c2 = upper->plane_first[fu.send_plane + 1] - upper->plane_first[fu.send_plane];
+    const long long d2 = lower->plane_first[fl.recv_plane + 1] - lower->plane_first[fl.recv_plane];
+    if (a != b || c2 != d2)
+        return fail(lower, LBM_EINVAL, "the planes at the face differ between the slabs (not adjacent slabs of one box)");
+    const size_t es = elem_of(lower);
+    const size_t nl = (size_t)lower->n_store, nu = (size_t)upper->n_store;
+    char* sl = static_cast<char*>(lower->f(lower->cur));
+    char* su = static_cast<char*>(upper->f(upper->cur));
+    int up[27], dn[27];
+    const int nup = dirs_with_cz(lower->grid.q, +1, up), ndn = dirs_with_cz(lower->grid.q, -1, dn);
+    HaloCopy H{};
+    H.elem = (int)es;
+    for (int k = 0; k < nup; ++k) {  // lower's top interior plane -> upper's lower halo, c_z = +1
+        H.src[H.ntask] = sl + ((size_t)up[k] * nl + (size_t)lower->plane_first[fl.send_plane]) * es;
+        H.dst[H.ntask] = su + ((size_t)up[k] * nu + (size_t)upper->plane_first[fu.recv_plane]) * es;
+        H.count[H.ntask++] = a;
+    }
+    for (int k = 0; k < ndn; ++k) {  // upper's first interior plane -> lower's upper halo, c_z = -1
+        H.src[H.ntask] = su + ((size_t)dn[k] * nu + (size_t)upper->plane_first[fu.send_plane]) * es;
+        H.dst[H.ntask] = sl + ((size_t)dn[k] * nl + (size_t)lower->plane_first[fl.recv_plane]) * es;
+        H.count[H.ntask++] = c2;
+    }
+    const cudaError_t e = launch_halo_copy(H, lower->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(lower, e, "halo exchange");
 }
 
 // ---------------------------------------------------------------------------

@@ -33,8 +33,9 @@ namespace lbm {
 // its source y - c_i (solid, box wall, or an open face); bits 27-28 cell type;
 // bit 29 set when some fluid neighbour has a different porosity; bit 30 set
 // when the cell lies on a periodic face; bit 31 marks a ghost slot (a solid
-// cell inside a packed span), whose bit 0 asks for zero stores (it shares an
-// aligned 8-slot group with a fluid slot).
+// cell inside a packed span, or any slot of a halo plane of a z-slab, whose
+// state the neighbouring slab provides), whose bit 0 asks for zero stores (it
+// shares an aligned 8-slot group with a fluid slot).
 constexpr uint32_t kTypeShift = 27;
 constexpr uint32_t kPorousBit = 1u << 29;
 constexpr uint32_t kWrapBit = 1u << 30;

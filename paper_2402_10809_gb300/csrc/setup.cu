@@ -240,6 +240,13 @@ __global__ void fill_f32(float* p, long long n, float v)
     if (i < n) p[i] = v;
 }
 
+// v into p[0..n).
+__global__ void fill_u32(uint32_t* p, long long n, uint32_t v)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
 // Number of non-ghost slots whose region byte (dense) is set; with wall_bits
 // nonzero only plain fluid cells with a wall link (mask & wall_bits) count.
 __global__ void region_count(const uint32_t* __restrict__ rows, const int* __restrict__ rowbase,
@@ -267,6 +274,20 @@ __global__ void scatter_f64(const uint32_t* __restrict__ rows, const int* __rest
     if (p >= n_store || (mask[p] & kGhostBit)) return;
     const uint32_t r = rows[p];
     dst[(long long)(p - rowbase[r]) + (long long)nx * r] = src[p];
+}
+
+// Task blockIdx.y of a halo copy, grid-strided over its elements.
+__global__ void halo_copy(const HaloCopy H)
+{
+    const int k = blockIdx.y;
+    if (k >= H.ntask) return;
+    const long long n = H.count[k];
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        if (H.elem == 4)
+            static_cast<uint32_t*>(H.dst[k])[e] = static_cast<const uint32_t*>(H.src[k])[e];
+        else
+            static_cast<uint16_t*>(H.dst[k])[e] = static_cast<const uint16_t*>(H.src[k])[e];
+    }
 }
 
 // Host launchers (kernel templates cannot be launched across translation units).
@@ -307,6 +328,13 @@ cudaError_t launch_fill_f32(float* p, long long n, float v, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_fill_u32(uint32_t* p, long long n, uint32_t v, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    fill_u32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_region_count(const uint32_t* rows, const int* rowbase, const uint32_t* mask, int n_store, int nx,
                                 const uint8_t* region, uint32_t wall_bits, unsigned long long* out, cudaStream_t s)
 {
@@ -321,6 +349,17 @@ cudaError_t launch_scatter_f64(const uint32_t* rows, const int* rowbase, const u
 {
     if (n_store == 0) return cudaSuccess;
     scatter_f64<<<(n_store + 255) / 256, 256, 0, s>>>(rows, rowbase, mask, n_store, nx, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_copy(const HaloCopy& H, cudaStream_t s)
+{
+    long long most = 0;
+    for (int k = 0; k < H.ntask; ++k) most = H.count[k] > most ? H.count[k] : most;
+    if (H.ntask == 0 || most == 0) return cudaSuccess;
+    const long long bx = (most + 255) / 256;
+    dim3 grid((unsigned)(bx < 1024 ? bx : 1024), (unsigned)H.ntask);
+    halo_copy<<<grid, 256, 0, s>>>(H);
     return cudaGetLastError();
 }
 

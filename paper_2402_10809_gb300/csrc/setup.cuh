@@ -44,10 +44,24 @@ cudaError_t launch_setup_slots(const float* phi, int nx, int nrows, const int* r
 cudaError_t launch_setup_mask(int q, const SetupParams& S, cudaStream_t s);
 cudaError_t launch_diag_finish(const double* partials, int nblk, double* out, cudaStream_t s);
 cudaError_t launch_fill_f32(float* p, long long n, float v, cudaStream_t s);
+cudaError_t launch_fill_u32(uint32_t* p, long long n, uint32_t v, cudaStream_t s);
 cudaError_t launch_region_count(const uint32_t* rows, const int* rowbase, const uint32_t* mask, int n_store, int nx,
                                 const uint8_t* region, uint32_t wall_bits, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_scatter_f64(const uint32_t* rows, const int* rowbase, const uint32_t* mask, int n_store, int nx,
                                const double* src, double* dst, cudaStream_t s);
+
+// Copies of the populations that cross a z-slab face (api.cu: lbm_halo_pack,
+// lbm_halo_unpack, lbm_halo_exchange): task k copies count[k] elements of
+// elem bytes (2 or 4) from src[k] to dst[k]; up to 18 tasks in one launch.
+constexpr int kHaloTasks = 18;
+struct HaloCopy {
+    const void* src[kHaloTasks];
+    void* dst[kHaloTasks];
+    long long count[kHaloTasks];
+    int ntask;
+    int elem;
+};
+cudaError_t launch_halo_copy(const HaloCopy& H, cudaStream_t s);
 
 // Volume-averaged porosity of a wire mask (porosity.cu): three sliding-window
 // passes through the caller's scratch (ws_x: N bytes, ws_y: N uint16).  The x

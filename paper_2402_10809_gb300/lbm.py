@@ -24,7 +24,8 @@ SYMBOLS = ["lbm_list_length", "lbm_workspace_size", "lbm_init", "lbm_step", "lbm
            "lbm_state_size", "lbm_save", "lbm_load", "lbm_time", "lbm_fluid_count", "lbm_last_error",
            "lbm_destroy", "lbm_adjoint_workspace_size", "lbm_adjoint", "lbm_wall_shear",
            "lbm_porosity_workspace_size", "lbm_porosity_average", "lbm_anisotropy_buffer_size",
-           "lbm_set_anisotropy"]
+           "lbm_set_anisotropy", "lbm_slab_bounds", "lbm_plane_slots", "lbm_set_halo", "lbm_halo_message_size",
+           "lbm_halo_pack", "lbm_halo_unpack", "lbm_halo_exchange"]
 
 
 class lbm_grid(C.Structure):
@@ -118,6 +119,20 @@ def load(build_if_missing=True):
     L.lbm_porosity_average.restype = C.c_int
     L.lbm_porosity_average.argtypes = [C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_int32, C.c_float, vp, vp,
                                        C.c_size_t, vp]
+    L.lbm_slab_bounds.restype = C.c_int
+    L.lbm_slab_bounds.argtypes = [P(lbm_grid), vp, C.c_int32, P(C.c_int32)]
+    L.lbm_plane_slots.restype = C.c_int
+    L.lbm_plane_slots.argtypes = [P(lbm_grid), vp, C.c_int32, P(C.c_int64), P(C.c_int64)]
+    L.lbm_set_halo.restype = C.c_int
+    L.lbm_set_halo.argtypes = [vp, C.c_int32, C.c_int32]
+    L.lbm_halo_message_size.restype = C.c_size_t
+    L.lbm_halo_message_size.argtypes = [vp, C.c_int32]
+    L.lbm_halo_pack.restype = C.c_int
+    L.lbm_halo_pack.argtypes = [vp, C.c_int32, vp]
+    L.lbm_halo_unpack.restype = C.c_int
+    L.lbm_halo_unpack.argtypes = [vp, C.c_int32, vp]
+    L.lbm_halo_exchange.restype = C.c_int
+    L.lbm_halo_exchange.argtypes = [vp, vp]
     L.lbm_destroy.restype = None
     L.lbm_destroy.argtypes = [vp]
     _lib = L
@@ -264,6 +279,44 @@ def lbm_set_anisotropy(ctx, shape, buffer, buffer_bytes, max_iter, tol):
     """shape / buffer: device addresses (shape 0 returns to the isotropic closure)."""
     _check(ctx, load().lbm_set_anisotropy(ctx, C.c_void_p(shape or None), C.c_void_p(buffer or None),
                                           C.c_size_t(buffer_bytes), int(max_iter), C.c_float(tol)))
+
+
+def lbm_slab_bounds(grid, flags_host, nslabs):
+    """z0 of each of nslabs balanced z-slabs plus nz (host only)."""
+    out = (C.c_int32 * (int(nslabs) + 1))()
+    st = load().lbm_slab_bounds(C.byref(grid), C.c_void_p(flags_host), int(nslabs), out)
+    if st != LBM_OK:
+        raise LBMError(st, "lbm_slab_bounds")
+    return [int(v) for v in out]
+
+
+def lbm_plane_slots(grid, flags_host, z):
+    """(first slot, slot count) of z-plane z in the packed layout (host only)."""
+    first, count = C.c_int64(), C.c_int64()
+    st = load().lbm_plane_slots(C.byref(grid), C.c_void_p(flags_host), int(z), C.byref(first), C.byref(count))
+    if st != LBM_OK:
+        raise LBMError(st, "lbm_plane_slots")
+    return int(first.value), int(count.value)
+
+
+def lbm_set_halo(ctx, lo_planes, hi_planes):
+    _check(ctx, load().lbm_set_halo(ctx, int(lo_planes), int(hi_planes)))
+
+
+def lbm_halo_message_size(ctx, side):
+    return int(load().lbm_halo_message_size(ctx, int(side)))
+
+
+def lbm_halo_pack(ctx, side, dst):
+    _check(ctx, load().lbm_halo_pack(ctx, int(side), C.c_void_p(dst)))
+
+
+def lbm_halo_unpack(ctx, side, src):
+    _check(ctx, load().lbm_halo_unpack(ctx, int(side), C.c_void_p(src)))
+
+
+def lbm_halo_exchange(lower, upper):
+    _check(lower, load().lbm_halo_exchange(lower, upper))
 
 
 def lbm_porosity_workspace_size(nx, ny, nz):
