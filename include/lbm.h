@@ -299,6 +299,24 @@ lbm_status lbm_porosity_average(int32_t nx, int32_t ny, int32_t nz, const uint8_
                                 int32_t window, float phi_min, float* phi, void* workspace, size_t workspace_bytes,
                                 void* cuda_stream);
 
+/* L2 residency of the time step (no counterpart in the paper; a property of
+ * the GPU execution).  Every step reads the per-slot words (row id, link mask,
+ * omega, porosity: 16 bytes per slot) while the populations stream past them.
+ * lbm_init keeps up to a quarter of the L2 cache's worth of them in its
+ * persisting part through an access-policy window on the step and reverse-
+ * step launches, raising the process's CUDA limit
+ * cudaLimitPersistingL2CacheSize to hold the window (never lowering it; a
+ * limit of the process's context, gone when the process exits).  lbm_step
+ * and lbm_adjoint of a context first return the persisting lines of the
+ * context that used them before to normal (cudaCtxResetPersistingL2Cache), and
+ * lbm_destroy those of its own, so contexts do not crowd each other out.
+ *  - lbm_set_l2_window: max_bytes < 0 the default (a quarter of the L2),
+ *    0 no window, > 0 at most that many bytes.  Results are identical either
+ *    way.
+ *  - lbm_l2_window_bytes: the window in bytes (0 none; -1 bad context). */
+lbm_status lbm_set_l2_window(lbm_ctx* ctx, int64_t max_bytes);
+int64_t lbm_l2_window_bytes(const lbm_ctx* ctx);
+
 /* Every check_every steps of later lbm_step calls, run the non-finite count of
  * lbm_diag and return LBM_EUNSTABLE when it is nonzero (0 = never, default). */
 lbm_status lbm_set_check(lbm_ctx* ctx, int32_t check_every);

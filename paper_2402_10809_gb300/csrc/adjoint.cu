@@ -28,6 +28,34 @@
 
 namespace lbm {
 
+namespace {
+// A reverse-step launch with the forward step's L2 window (the row records and
+// per-slot words that every reverse step reads too), when the context has one.
+template <int TPS, bool AN>
+cudaError_t launch_reverse(int grid, size_t smem, const AdjParams& A, cudaStream_t s)
+{
+    if (A.F.l2_bytes == 0) {
+        adjoint_kernel<LBM_Q, LBM_T, TPS, AN><<<grid, kBlock, smem, s>>>(A);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    at[0].val.accessPolicyWindow.base_ptr = const_cast<void*>(A.F.l2_base);
+    at[0].val.accessPolicyWindow.num_bytes = A.F.l2_bytes;
+    at[0].val.accessPolicyWindow.hitRatio = A.F.l2_hit;
+    at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, adjoint_kernel<LBM_Q, LBM_T, TPS, AN>, A);
+}
+}  // namespace
+
 // what = 0: reverse time step; 1: outlet fix-up; 2: outlet ordinals (once per call).
 cudaError_t LBM_LAUNCHER(int what, const AdjParams& A, cudaStream_t s)
 {
@@ -50,16 +78,9 @@ cudaError_t LBM_LAUNCHER(int what, const AdjParams& A, cudaStream_t s)
         // grids of up to two waves of the 512-thread variant (152 SMs) take
         // the 384-thread one
         const bool small = grid <= 2 * 152 * (512 / kBlock);
-        if (A.F.aniso) {
-            if (small)
-                adjoint_kernel<LBM_Q, LBM_T, 384, true><<<grid, kBlock, smem, s>>>(A);
-            else
-                adjoint_kernel<LBM_Q, LBM_T, 512, true><<<grid, kBlock, smem, s>>>(A);
-        } else if (small) {
-            adjoint_kernel<LBM_Q, LBM_T, 384, false><<<grid, kBlock, smem, s>>>(A);
-        } else {
-            adjoint_kernel<LBM_Q, LBM_T, 512, false><<<grid, kBlock, smem, s>>>(A);
-        }
+        if (A.F.aniso)
+            return small ? launch_reverse<384, true>(grid, smem, A, s) : launch_reverse<512, true>(grid, smem, A, s);
+        return small ? launch_reverse<384, false>(grid, smem, A, s) : launch_reverse<512, false>(grid, smem, A, s);
     } else if (what == 1) {
         if (A.n_out == 0) return cudaSuccess;
         adjoint_outlet_fixup<LBM_Q><<<(A.n_out + 127) / 128, 128, 0, s>>>(A);

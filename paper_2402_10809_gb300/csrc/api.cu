@@ -186,6 +186,81 @@ static lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where)
         if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
     } while (0)
 
+// The L2 residency window of the step launches: the per-slot words (row id,
+// mask, omega, porosity), which every step reads and which lie back to back
+// in the workspace.  At most `cap` bytes of them (a quarter of the L2 by
+// default: more would take the L2 from the streaming populations); the
+// process's persisting-L2 limit (a per-process CUDA limit) is raised to hold
+// the window, never lowered; the hit ratio covers what the limit allows.
+// Devices without persisting L2 get no window.
+static cudaError_t l2_window(lbm_ctx* c, long long cap)
+{
+    Params& P = c->base;
+    P.l2_base = nullptr;
+    P.l2_bytes = 0;
+    P.l2_hit = 0.0f;
+    if (cap == 0 || c->n_store == 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int max_persist = 0, max_window = 0, l2 = 0;
+    e = cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    if (e != cudaSuccess) return e;
+    if (max_persist <= 0 || max_window <= 0) return cudaSuccess;
+    if (cap < 0) cap = l2 / 4;
+    size_t win = c->L.bnd_prof - c->L.rows;
+    if (win > (size_t)cap) win = (size_t)cap;
+    if (win > (size_t)max_window) win = (size_t)max_window;
+    size_t cur = 0;
+    e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    if (e != cudaSuccess) return e;
+    const size_t lim = win < (size_t)max_persist ? win : (size_t)max_persist;
+    if (cur < lim) {
+        e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, lim);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+        if (e != cudaSuccess) return e;
+    }
+    P.l2_base = c->ws + c->L.rows;
+    P.l2_bytes = win;
+    P.l2_hit = (float)((double)(cur < win ? cur : win) / (double)win);
+    return cudaSuccess;
+}
+
+// The context whose window last claimed the persisting part of L2, per
+// device.  When another context starts stepping, the persisting lines of the
+// previous one are returned to normal (cudaCtxResetPersistingL2Cache), so that
+// a context's window never competes with stale lines of another.
+static constexpr int kL2Devices = 64;
+static const lbm_ctx* g_l2_owner[kL2Devices] = {};
+
+static cudaError_t l2_claim(const lbm_ctx* c)
+{
+    if (c->base.l2_bytes == 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kL2Devices) return e;
+    if (g_l2_owner[dev] == c) return cudaSuccess;
+    e = cudaCtxResetPersistingL2Cache();
+    if (e == cudaSuccess) g_l2_owner[dev] = c;
+    return e;
+}
+
+static void l2_release(const lbm_ctx* c)
+{
+    for (int d = 0; d < kL2Devices; ++d) {
+        if (g_l2_owner[d] == c) {
+            int cur = -1;
+            if (cudaGetDevice(&cur) == cudaSuccess && cur == d) cudaCtxResetPersistingL2Cache();
+            g_l2_owner[d] = nullptr;
+        }
+    }
+}
+
 extern "C" size_t lbm_workspace_size(const lbm_grid* grid, int64_t n_list)
 {
     if (!grid_ok(grid)) return 0;
@@ -459,6 +534,7 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     P.rho_out = (float)bc->rho_out;
     P.omega = c->at<float>(c->L.omega);
     c->omega0 = (float)(2.0 / (6.0 * mu0 + 1.0));  // omega(mu0) at rho = 1
+    LBM_CUDA(l2_window(c, -1), "L2 residency window");
 
     // initial state: rest equilibrium (zero deviations)
     const size_t fb = (size_t)grid->q * c->n_store * elem_size(grid->storage);
@@ -475,6 +551,7 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, int32_t n)
     if (!c) return LBM_EINVAL;
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
     if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    if (n > 0) LBM_CUDA(l2_claim(c), "claim the persisting L2");
     for (int32_t s = 0; s < n; ++s) {
         Params P = c->base;
         P.fsrc = c->f(c->cur);
@@ -655,6 +732,16 @@ extern "C" lbm_status lbm_porosity_average(int32_t nx, int32_t ny, int32_t nz, c
     return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
+extern "C" lbm_status lbm_set_l2_window(lbm_ctx* c, int64_t max_bytes)
+{
+    if (!c) return LBM_EINVAL;
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    LBM_CUDA(l2_window(c, max_bytes), "L2 residency window");
+    return LBM_OK;
+}
+
+extern "C" int64_t lbm_l2_window_bytes(const lbm_ctx* c) { return c && c->ready ? (int64_t)c->base.l2_bytes : -1; }
+
 extern "C" lbm_status lbm_set_check(lbm_ctx* c, int32_t check_every)
 {
     if (!c) return LBM_EINVAL;
@@ -728,7 +815,11 @@ extern "C" lbm_status lbm_load(lbm_ctx* c, const void* src, size_t bytes, int32_
 extern "C" int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 extern "C" int64_t lbm_fluid_count(const lbm_ctx* c) { return c ? c->n_store - c->n_ghost : -1; }
 extern "C" const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
-extern "C" void lbm_destroy(lbm_ctx* c) { delete c; }
+extern "C" void lbm_destroy(lbm_ctx* c)
+{
+    if (c) l2_release(c);
+    delete c;
+}
 
 // ---------------------------------------------------------------------------
 // Discrete adjoint: d J / d phi of the sac kinetic-energy objective by a
@@ -856,6 +947,7 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, int32_t T, int32_t K, int32_t obje
         return fail(c, LBM_EINVAL, objective == 1 ? "the objective region holds no fluid cell next to a wall"
                                                   : "the objective region holds no fluid cell");
     const int nblk = total_blocks(B);
+    LBM_CUDA(l2_claim(c), "claim the persisting L2");
     LBM_CUDA(cudaMemsetAsync(grad, 0, N * 8, st), "clear gradient");
     LBM_CUDA(cudaMemsetAsync(gphi, 0, n * 8, st), "clear packed gradient");
     LBM_CUDA(cudaMemsetAsync(Cs(0), 0, AL.sbytes, st), "rest state");

@@ -99,6 +99,12 @@ struct Params {
     const float* aniso;
     int aniso_iters;
     float aniso_tol;
+    // L2 residency of the step: [l2_base, l2_base + l2_bytes) (the row records
+    // and the per-slot words) is kept in the persisting part of L2 with hit
+    // ratio l2_hit; l2_bytes = 0 launches without a window
+    const void* l2_base;
+    size_t l2_bytes;
+    float l2_hit;
     // diagnostics
     const uint8_t* region;    // dense, may be null
     double* partials;         // [gridDim.x][kDiagSlots]

@@ -29,10 +29,36 @@
 
 namespace lbm {
 
+namespace {
+// A time-step launch with the L2 access-policy window of P: the row records
+// and per-slot words it covers are read by every step, so they stay resident
+// in the persisting part of L2 while the populations stream past them.
+template <bool AN>
+cudaError_t launch_step_window(int grid, const Params& P, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    at[0].val.accessPolicyWindow.base_ptr = const_cast<void*>(P.l2_base);
+    at[0].val.accessPolicyWindow.num_bytes = P.l2_bytes;
+    at[0].val.accessPolicyWindow.hitRatio = P.l2_hit;
+    at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, lbm_kernel<LBM_Q, LBM_T, kModeStep, AN>, P);
+}
+}  // namespace
+
 cudaError_t LBM_LAUNCHER(int mode, const Params& P, cudaStream_t s)
 {
     const int grid = total_blocks(P);
     if (grid == 0) return cudaSuccess;
+    if (mode == kModeStep && P.l2_bytes > 0)
+        return P.aniso ? launch_step_window<true>(grid, P, s) : launch_step_window<false>(grid, P, s);
     if (P.aniso) {
         switch (mode) {
             case kModeStep: lbm_kernel<LBM_Q, LBM_T, kModeStep, true><<<grid, kBlock, 0, s>>>(P); break;

@@ -25,7 +25,8 @@ SYMBOLS = ["lbm_list_length", "lbm_workspace_size", "lbm_init", "lbm_step", "lbm
            "lbm_destroy", "lbm_adjoint_workspace_size", "lbm_adjoint", "lbm_wall_shear",
            "lbm_porosity_workspace_size", "lbm_porosity_average", "lbm_anisotropy_buffer_size",
            "lbm_set_anisotropy", "lbm_slab_bounds", "lbm_plane_slots", "lbm_set_halo", "lbm_halo_message_size",
-           "lbm_halo_pack", "lbm_halo_unpack", "lbm_halo_exchange"]
+           "lbm_halo_pack", "lbm_halo_unpack", "lbm_halo_exchange", "lbm_set_l2_window",
+           "lbm_l2_window_bytes"]
 
 
 class lbm_grid(C.Structure):
@@ -133,6 +134,10 @@ def load(build_if_missing=True):
     L.lbm_halo_unpack.argtypes = [vp, C.c_int32, vp]
     L.lbm_halo_exchange.restype = C.c_int
     L.lbm_halo_exchange.argtypes = [vp, vp]
+    L.lbm_set_l2_window.restype = C.c_int
+    L.lbm_set_l2_window.argtypes = [vp, C.c_int64]
+    L.lbm_l2_window_bytes.restype = C.c_int64
+    L.lbm_l2_window_bytes.argtypes = [vp]
     L.lbm_destroy.restype = None
     L.lbm_destroy.argtypes = [vp]
     _lib = L
@@ -220,6 +225,15 @@ def lbm_diag_noalloc(ctx, region_device):
 
 def lbm_wall_shear(ctx, wss, dst_on_device):
     _check(ctx, load().lbm_wall_shear(ctx, C.c_void_p(wss), int(dst_on_device)))
+
+
+def lbm_set_l2_window(ctx, max_bytes=-1):
+    """max_bytes < 0: the default window; 0: none; > 0: at most that many bytes."""
+    _check(ctx, load().lbm_set_l2_window(ctx, int(max_bytes)))
+
+
+def lbm_l2_window_bytes(ctx):
+    return int(load().lbm_l2_window_bytes(ctx))
 
 
 def lbm_set_check(ctx, check_every):

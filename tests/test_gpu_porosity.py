@@ -2,11 +2,11 @@
 porosity (oracle/porosity.py).  The count is exact integer work and the
 quotient is correctly rounded on both sides, so the comparison is bit-exact.
 
-Cases: odd and even windows, a window wider than the box, window 1 (the wire
-itself), ragged x extents (scalar path), segments along y and z that end
-mid-way, unaligned output (scalar path with a multiple-of-4 x extent), solid
-override; the 512^3 box of the coil study at the paper's 28-cell window on
-sampled cells; the documented argument errors.
+Cases: odd and even windows up to 40 cells, a window wider than the box,
+window 1 (the wire itself), ragged x extents (scalar path), segments along y
+and z that end mid-way, unaligned output (scalar path), solid override; the
+512^3 box of the coil study at the paper's 28-cell window on sampled cells;
+the documented argument errors.
 """
 
 import numpy as np
@@ -44,6 +44,9 @@ CASES = [
     ((16, 8, 12), 1, 0.0, 0.5, False),
     ((3, 2, 1), 2, 0.1, 0.5, True),
     ((200, 3, 130), 9, 0.2, 0.6, False),
+    ((96, 70, 300), 32, 0.05, 0.02, True),   # long z: several running-sum segments per line
+    ((70, 45, 60), 40, 0.05, 0.3, True),
+    ((68, 40, 33), 33, 0.0, 0.1, False),
 ]
 
 
@@ -58,11 +61,13 @@ def test_matches_oracle_exactly(lbm, dims, window, phi_min, density, with_flags)
     assert got.dtype == np.float32 and np.array_equal(got.view(np.uint32), ref.view(np.uint32))
 
 
-def test_unaligned_output_takes_the_scalar_path(lbm):
+@pytest.mark.parametrize("window", [6, 36])
+def test_unaligned_output(lbm, window):
+    """An output pointer off the 16-byte grid takes the scalar form of the passes."""
     rng = np.random.default_rng(11)
     wire = (rng.random((20, 12, 32)) < 0.3).astype(np.uint8)
-    ref = porosity_average(wire, 6, 0.05)
-    assert np.array_equal(gpu_phi(lbm, wire, 6, 0.05, offset=1), ref)
+    ref = porosity_average(wire, window, 0.05)
+    assert np.array_equal(gpu_phi(lbm, wire, window, 0.05, offset=1), ref)
 
 
 def test_coil_study_box_sampled(lbm):
