@@ -29,29 +29,31 @@
 namespace lbm {
 
 namespace {
-// A reverse-step launch with the forward step's L2 window (the row records and
-// per-slot words that every reverse step reads too), when the context has one.
+// A reverse-step launch: programmatic stream serialization, as for the time
+// steps, and the forward step's L2 window (the per-slot words every reverse
+// step reads too) when the context has one.
 template <int TPS, bool AN>
 cudaError_t launch_reverse(int grid, size_t smem, const AdjParams& A, cudaStream_t s)
 {
-    if (A.F.l2_bytes == 0) {
-        adjoint_kernel<LBM_Q, LBM_T, TPS, AN><<<grid, kBlock, smem, s>>>(A);
-        return cudaGetLastError();
-    }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kBlock);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeAccessPolicyWindow;
-    at[0].val.accessPolicyWindow.base_ptr = const_cast<void*>(A.F.l2_base);
-    at[0].val.accessPolicyWindow.num_bytes = A.F.l2_bytes;
-    at[0].val.accessPolicyWindow.hitRatio = A.F.l2_hit;
-    at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-    at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    if (A.F.l2_bytes > 0) {
+        at[1].id = cudaLaunchAttributeAccessPolicyWindow;
+        at[1].val.accessPolicyWindow.base_ptr = const_cast<void*>(A.F.l2_base);
+        at[1].val.accessPolicyWindow.num_bytes = A.F.l2_bytes;
+        at[1].val.accessPolicyWindow.hitRatio = A.F.l2_hit;
+        at[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        at[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.numAttrs = 2;
+    }
     return cudaLaunchKernelEx(&cfg, adjoint_kernel<LBM_Q, LBM_T, TPS, AN>, A);
 }
 }  // namespace

@@ -697,7 +697,11 @@ __global__ void __launch_bounds__(kBlock, TPS / kBlock) adjoint_kernel(const Adj
     volatile float* lampark = park + Q * kBlock;
     volatile float* dpark = park + 2 * Q * kBlock;
     double jv = 0.0;
+    // programmatic launch (see lbm_kernel): static words before the wait,
+    // everything a previous kernel writes after it
+    grid_dependents_launch();
     if ((int)blockIdx.x < nbg) {
+        grid_dependency_wait();
         const int k = (int)blockIdx.x * P.gen_block + (int)threadIdx.x;
         if ((int)threadIdx.x < P.gen_block && k < P.n_general) {
             const int p = (int)P.general[k];
@@ -705,12 +709,14 @@ __global__ void __launch_bounds__(kBlock, TPS / kBlock) adjoint_kernel(const Adj
         }
     } else {
         const int p = ((int)blockIdx.x - nbg) * kBlock + (int)threadIdx.x;
+        if (p >= P.n_store) grid_dependency_wait();
         if (p < P.n_store) {
             // every per-slot word of the cell at once (one memory latency
             // before the row record instead of one per word)
             const uint32_t mask = ld_early_u32(P.mask + p);
             const uint32_t row = ld_early_u32(P.rows + p);
             const float phi = ld_early_nc(P.phi + p);
+            grid_dependency_wait();
             const float om = ld_early_nc(P.omega + p);
             const float mu = A.first ? 0.0f : ld_early(A.mu + p);
             // ghost slots hold no state; general cells belong to the general blocks

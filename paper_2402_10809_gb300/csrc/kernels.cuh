@@ -161,6 +161,14 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Programmatic dependent launch of the time steps: a step's blocks may start
+// while the previous step's last blocks finish.  Before grid_dependency_wait()
+// a step reads only data no step writes (mask, row id, porosity, row
+// records); the wait returns once the previous step has completed and its
+// writes are visible.  Outside a programmatic launch both are no-ops.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // Loads issued in program order (inline PTX, so that the compiler neither
 // sinks them to their first use nor places them behind a branch): a lean
 // cell requests all its per-slot words before its first dependent load, so
@@ -800,7 +808,10 @@ __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS) lbm_kernel(const Param
     // dv: 0 sum phi, 1 sum (phi rho - phi), 2 kinetic energy, 3 region sum |u|,
     //     4 region count, 5 max |u|, 6 min omega, 7 max omega, 8 non-finite count
     volatile float* park = park_column<Q, MODE>();
+    // the next step may be scheduled once every block of this one has started
+    if (MODE == kModeStep) grid_dependents_launch();
     if ((int)blockIdx.x < nbg) {
+        if (MODE == kModeStep) grid_dependency_wait();
         const int k = (int)blockIdx.x * P.gen_block + (int)threadIdx.x;
         if ((int)threadIdx.x < P.gen_block && k < P.n_general) {
             const int p = (int)P.general[k];
@@ -814,6 +825,9 @@ __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS) lbm_kernel(const Param
             const uint32_t mask = ld_early_u32(P.mask + p);
             const uint32_t row = ld_early_u32(P.rows + p);
             const float phi = ld_early_nc(P.phi + p);
+            // omega and the populations are the previous step's outputs, and
+            // this step's stores go to the buffer the previous step read
+            if (MODE == kModeStep) grid_dependency_wait();
             const float om = ld_early(P.omega + p);
             lean_body<Q, T, MODE, AN>(P, p, mask, dv, park, row, phi, om);
         }

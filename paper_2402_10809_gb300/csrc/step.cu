@@ -30,25 +30,32 @@
 namespace lbm {
 
 namespace {
-// A time-step launch with the L2 access-policy window of P: the row records
-// and per-slot words it covers are read by every step, so they stay resident
-// in the persisting part of L2 while the populations stream past them.
+// A time-step launch: programmatic stream serialization (the step's blocks may
+// start while the previous kernel on the stream finishes; lbm_kernel waits
+// for it before its first dependent access) and, when P has one, the L2
+// access-policy window of the row records and per-slot words, which every
+// step reads, so that they stay resident while the populations stream past.
 template <bool AN>
-cudaError_t launch_step_window(int grid, const Params& P, cudaStream_t s)
+cudaError_t launch_step(int grid, const Params& P, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kBlock);
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeAccessPolicyWindow;
-    at[0].val.accessPolicyWindow.base_ptr = const_cast<void*>(P.l2_base);
-    at[0].val.accessPolicyWindow.num_bytes = P.l2_bytes;
-    at[0].val.accessPolicyWindow.hitRatio = P.l2_hit;
-    at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-    at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    if (P.l2_bytes > 0) {
+        at[1].id = cudaLaunchAttributeAccessPolicyWindow;
+        at[1].val.accessPolicyWindow.base_ptr = const_cast<void*>(P.l2_base);
+        at[1].val.accessPolicyWindow.num_bytes = P.l2_bytes;
+        at[1].val.accessPolicyWindow.hitRatio = P.l2_hit;
+        at[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        at[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.numAttrs = 2;
+    }
     return cudaLaunchKernelEx(&cfg, lbm_kernel<LBM_Q, LBM_T, kModeStep, AN>, P);
 }
 }  // namespace
@@ -57,18 +64,15 @@ cudaError_t LBM_LAUNCHER(int mode, const Params& P, cudaStream_t s)
 {
     const int grid = total_blocks(P);
     if (grid == 0) return cudaSuccess;
-    if (mode == kModeStep && P.l2_bytes > 0)
-        return P.aniso ? launch_step_window<true>(grid, P, s) : launch_step_window<false>(grid, P, s);
+    if (mode == kModeStep) return P.aniso ? launch_step<true>(grid, P, s) : launch_step<false>(grid, P, s);
     if (P.aniso) {
         switch (mode) {
-            case kModeStep: lbm_kernel<LBM_Q, LBM_T, kModeStep, true><<<grid, kBlock, 0, s>>>(P); break;
             case kModeMoments: lbm_kernel<LBM_Q, LBM_T, kModeMoments, true><<<grid, kBlock, 0, s>>>(P); break;
             default: lbm_kernel<LBM_Q, LBM_T, kModeDiag, true><<<grid, kBlock, 0, s>>>(P); break;
         }
         return cudaGetLastError();
     }
     switch (mode) {
-        case kModeStep: lbm_kernel<LBM_Q, LBM_T, kModeStep><<<grid, kBlock, 0, s>>>(P); break;
         case kModeMoments: lbm_kernel<LBM_Q, LBM_T, kModeMoments><<<grid, kBlock, 0, s>>>(P); break;
         default: lbm_kernel<LBM_Q, LBM_T, kModeDiag><<<grid, kBlock, 0, s>>>(P); break;
     }
