@@ -275,6 +275,34 @@ extern "C" int64_t lbm_list_length(const lbm_grid* grid, const uint8_t* flags)
     return host_spans(grid, flags, nullptr, nullptr);
 }
 
+// Dense index of every slot (-1 for ghost slots), for the calls that scatter
+// per-slot results to a host array; built from the device's row ids and masks
+// on first use.
+static lbm_status ensure_host_idx(lbm_ctx* c)
+{
+    if ((int)c->host_idx.size() == c->n_store) return LBM_OK;
+    const size_t n = (size_t)c->n_store;
+    std::vector<uint32_t> hm(n), hr(n);
+    std::vector<int> rb((size_t)c->grid.ny * c->grid.nz);
+    if (n > 0) {
+        LBM_CUDA(cudaMemcpyAsync(hm.data(), c->at<uint32_t>(c->L.mask), n * 4, cudaMemcpyDeviceToHost, c->stream),
+                 "copy masks");
+        LBM_CUDA(cudaMemcpyAsync(hr.data(), c->at<uint32_t>(c->L.rows), n * 4, cudaMemcpyDeviceToHost, c->stream),
+                 "copy row ids");
+        LBM_CUDA(cudaMemcpyAsync(rb.data(), c->at<int>(c->L.rowbase), rb.size() * 4, cudaMemcpyDeviceToHost,
+                                 c->stream), "copy row bases");
+        LBM_CUDA(cudaStreamSynchronize(c->stream), "copy sync");
+    }
+    std::vector<long long> idx(n, -1);
+    for (size_t p = 0; p < n; ++p) {
+        if (hm[p] & kGhostBit) continue;
+        const uint32_t r = hr[p];
+        idx[p] = (long long)((long long)p - rb[r]) + (long long)c->grid.nx * r;
+    }
+    c->host_idx.swap(idx);
+    return LBM_OK;
+}
+
 static lbm_status run_diag(lbm_ctx* c, const uint8_t* region_dev, double out[8])
 {
     Params P = c->base;
@@ -375,27 +403,12 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
         return fail(c, LBM_ENOMEM, "workspace smaller than lbm_workspace_size(grid, " + std::to_string(c->n_store) +
                                        "), the packed length of these flags");
     // per row: the bases of its nine neighbour rows, wrapped on periodic axes
-    // (0 outside the box: those links are never pulled), then y, z
-    std::vector<int> rownb((size_t)nrows * 12, 0);
-    for (int z = 0; z < nz; ++z) {
-        for (int y = 0; y < ny; ++y) {
-            const int r = y + ny * z;
-            int* e = &rownb[(size_t)r * 12];
-            for (int sz = -1; sz <= 1; ++sz)
-                for (int sy = -1; sy <= 1; ++sy) {
-                    int yy = y + sy, zz = z + sz;
-                    if (grid->periodic[1]) yy = (yy + ny) % ny;
-                    if (grid->periodic[2]) zz = (zz + nz) % nz;
-                    e[(sy + 1) + 3 * (sz + 1)] = (yy >= 0 && yy < ny && zz >= 0 && zz < nz) ? rowbase[yy + ny * zz] : 0;
-                }
-            e[9] = y;
-            e[10] = z;
-        }
-    }
+    // (0 outside the box: those links are never pulled), then y, z (device)
     LBM_CUDA(cudaMemcpyAsync(c->at<int>(c->L.rowbase), rowbase.data(), (size_t)nrows * 4, cudaMemcpyHostToDevice,
                              c->stream), "copy row bases");
-    LBM_CUDA(cudaMemcpyAsync(c->at<int>(c->L.rownb), rownb.data(), (size_t)nrows * 48, cudaMemcpyHostToDevice,
-                             c->stream), "copy row table");
+    LBM_CUDA(launch_setup_rownb(c->at<int>(c->L.rowbase), ny, nz, grid->periodic[1] ? 1 : 0,
+                                grid->periodic[2] ? 1 : 0, c->at<int>(c->L.rownb), c->stream),
+             "setup_rownb");
     LBM_CUDA(launch_setup_slots(c->at<float>(c->L.phi_dense), nx, nrows, c->at<int>(c->L.rowbase),
                                 c->at<int>(c->L.xmin), c->at<int>(c->L.ext), c->at<uint32_t>(c->L.rows),
                                 c->at<float>(c->L.phi), c->stream),
@@ -424,13 +437,10 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     LBM_CUDA(launch_setup_mask(grid->q, S, c->stream), "setup_mask");
     uint32_t errv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     LBM_CUDA(cudaMemcpyAsync(errv, errw, 32, cudaMemcpyDeviceToHost, c->stream), "copy error words");
-    std::vector<uint32_t> hmask(c->n_store), hrows(c->n_store);
-    if (c->n_store > 0) {
+    std::vector<uint32_t> hmask(c->n_store);
+    if (c->n_store > 0)
         LBM_CUDA(cudaMemcpyAsync(hmask.data(), S.mask, (size_t)c->n_store * 4, cudaMemcpyDeviceToHost, c->stream),
                  "copy masks");
-        LBM_CUDA(cudaMemcpyAsync(hrows.data(), S.rows, (size_t)c->n_store * 4, cudaMemcpyDeviceToHost, c->stream),
-                 "copy row ids");
-    }
     LBM_CUDA(cudaStreamSynchronize(c->stream), "setup sync");
     if (errv[0]) {
         float bad_phi;
@@ -451,24 +461,25 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
                     std::string("outlet cells must lie on the outlet face with porosity 1 and a fluid interior "
                                 "neighbour of porosity 1") + where);
     }
-    // host tables: dense index of every slot, ghost count, outlet slots
+    // host tables: ghost count, outlet slots, general list (the dense index of
+    // every slot is built on the first call that scatters to host memory)
     const bool wide = (unsigned long long)grid->q * (unsigned long long)c->n_store >= (1ull << 32);
-    c->host_idx.assign(c->n_store, -1);
+    c->host_idx.clear();
     c->out_slots.clear();
     c->general.clear();
     c->n_ghost = 0;
     c->n_in = 0;
     for (int p = 0; p < c->n_store; ++p) {
-        if (hmask[p] & kGhostBit) {
+        const uint32_t m = hmask[p];
+        if (!(m & (kGhostBit | kGeneralBits)) && !wide) continue;
+        if (m & kGhostBit) {
             ++c->n_ghost;
             continue;
         }
-        const uint32_t r = hrows[p];
-        c->host_idx[p] = (long long)(p - rowbase[r]) + (long long)nx * r;
-        const uint32_t type = (hmask[p] >> kTypeShift) & 3u;
+        const uint32_t type = (m >> kTypeShift) & 3u;
         if (type == kOutlet) c->out_slots.push_back((uint32_t)p);
         if (type == kInlet) ++c->n_in;
-        if (wide || (hmask[p] & kGeneralBits)) c->general.push_back((uint32_t)p);
+        c->general.push_back((uint32_t)p);
     }
     c->n_out = (int)c->out_slots.size();
     c->all_general = c->general;
@@ -605,6 +616,8 @@ extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho, float* u, float* shear
     P.o_omega = st + 5 * n;
     P.o_compact = 1;
     std::vector<float> h(6 * n);
+    const lbm_status hs = ensure_host_idx(c);
+    if (hs != LBM_OK) return hs;
     if (n > 0) {
         LBM_CUDA(launch(c->grid, kModeMoments, P, c->stream), "moments kernel");
         LBM_CUDA(cudaMemcpyAsync(h.data(), st, 6 * n * 4, cudaMemcpyDeviceToHost, c->stream), "moments copy");
@@ -654,6 +667,8 @@ extern "C" lbm_status lbm_wall_shear(lbm_ctx* c, float* wss, int32_t dst_on_devi
     const size_t n = (size_t)c->n_store;
     float* st = c->at<float>(c->L.staging);
     std::vector<float> h(n);
+    const lbm_status hs = ensure_host_idx(c);
+    if (hs != LBM_OK) return hs;
     if (n > 0) {
         LBM_CUDA(cudaMemsetAsync(st, 0, n * 4, c->stream), "clear wall shear");
         LBM_CUDA(launch_wall_shear(c->grid.q, c->grid.storage, P, st, 1, c->stream), "wall shear kernel");
@@ -1195,6 +1210,7 @@ extern "C" lbm_status lbm_set_halo(lbm_ctx* c, int32_t lo_planes, int32_t hi_pla
                                  cudaMemcpyHostToDevice, c->stream), "copy general list");
     LBM_CUDA(cudaStreamSynchronize(c->stream), "halo set-up sync");
     c->base.n_general = (int)c->general.size();
+    c->host_idx.clear();  // halo slots scatter nothing to host outputs
     c->halo_lo = lo_planes;
     c->halo_hi = hi_planes;
     return LBM_OK;

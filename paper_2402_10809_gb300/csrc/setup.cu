@@ -91,20 +91,42 @@ __device__ uint32_t link_mask(const SetupParams& S, int x, int y, int z, int typ
     if ((S.periodic[0] && (x == 0 || x == S.nx - 1)) || (S.periodic[1] && (y == 0 || y == S.ny - 1)) ||
         (S.periodic[2] && (z == 0 || z == S.nz - 1)))
         m |= kWrapBit;
-    for (int i = 0; i < Q; ++i) {
-        long long s;
-        int ax, sd;
-        if (!step_to(S, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i), &s, &ax, &sd) || !fluid_flag(S.flags[s]))
-            m |= 1u << i;
-    }
+    // one visit per neighbour (x, y, z) + c_i: it is the pull source of
+    // direction opp(i) (bit opp(i) set when it is not fluid or outside the
+    // box) and, when fluid with another porosity, makes the cell porous
     for (int i = 1; i < Q; ++i) {
         long long d;
         int ax, sd;
-        if (step_to(S, x, y, z, L::cx(i), L::cy(i), L::cz(i), &d, &ax, &sd) && fluid_flag(S.flags[d]) &&
-            S.phi[d] != phi)
-            m |= kPorousBit;
+        if (step_to(S, x, y, z, L::cx(i), L::cy(i), L::cz(i), &d, &ax, &sd) && fluid_flag(S.flags[d])) {
+            if (S.phi[d] != phi) m |= kPorousBit;
+        } else {
+            m |= 1u << opp(i);
+        }
     }
     return m;
+}
+
+// One thread per row (y, z): the bases of its nine neighbour rows
+// (y + sy, z + sz) at index (sy + 1) + 3 (sz + 1), wrapped on periodic axes,
+// 0 outside the box (those links are never pulled), then y, z, 0.
+__global__ void setup_rownb(const int* __restrict__ rowbase, int ny, int nz, int py, int pz, int* __restrict__ out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ny * nz) return;
+    const int y = r % ny, z = r / ny;
+    int* e = out + (size_t)r * 12;
+#pragma unroll
+    for (int sz = -1; sz <= 1; ++sz)
+#pragma unroll
+        for (int sy = -1; sy <= 1; ++sy) {
+            int yy = y + sy, zz = z + sz;
+            if (py) yy = (yy + ny) % ny;
+            if (pz) zz = (zz + nz) % nz;
+            e[(sy + 1) + 3 * (sz + 1)] = (yy >= 0 && yy < ny && zz >= 0 && zz < nz) ? rowbase[yy + ny * zz] : 0;
+        }
+    e[9] = y;
+    e[10] = z;
+    e[11] = 0;
 }
 
 // Dense index of slot q.
@@ -307,6 +329,14 @@ cudaError_t launch_setup_slots(const float* phi, int nx, int nrows, const int* r
     const int per_block = kSetupThreads / 32;
     setup_slots<<<(nrows + per_block - 1) / per_block, kSetupThreads, 0, s>>>(phi, nx, nrows, rowbase, xmin, ext,
                                                                               rows, phi_s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup_rownb(const int* rowbase, int ny, int nz, int py, int pz, int* out, cudaStream_t s)
+{
+    const int nrows = ny * nz;
+    if (nrows == 0) return cudaSuccess;
+    setup_rownb<<<(nrows + 255) / 256, 256, 0, s>>>(rowbase, ny, nz, py, pz, out);
     return cudaGetLastError();
 }
 

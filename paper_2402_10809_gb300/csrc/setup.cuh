@@ -41,6 +41,7 @@ cudaError_t launch_setup_rows(const uint8_t* flags, int nx, int nrows, int* xmin
                               cudaStream_t s);
 cudaError_t launch_setup_slots(const float* phi, int nx, int nrows, const int* rowbase, const int* xmin,
                                const int* ext, uint32_t* rows, float* phi_s, cudaStream_t s);
+cudaError_t launch_setup_rownb(const int* rowbase, int ny, int nz, int py, int pz, int* out, cudaStream_t s);
 cudaError_t launch_setup_mask(int q, const SetupParams& S, cudaStream_t s);
 cudaError_t launch_diag_finish(const double* partials, int nblk, double* out, cudaStream_t s);
 cudaError_t launch_fill_f32(float* p, long long n, float v, cudaStream_t s);
