@@ -435,12 +435,20 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     S.in_radius = bc->inlet_radius;
     S.err = errw;
     LBM_CUDA(launch_setup_mask(grid->q, S, c->stream), "setup_mask");
+    // slot classes per chunk of slots (device), for the host tables below;
+    // the staging area is free until the first host-output call
+    const bool wide = (unsigned long long)grid->q * (unsigned long long)c->n_store >= (1ull << 32);
+    const int nch = classify_chunks(c->n_store);
+    int4* cls_d = c->at<int4>(c->L.staging);
+    int2* off_d = reinterpret_cast<int2*>(cls_d + nch);
+    uint32_t* outl_d = reinterpret_cast<uint32_t*>(off_d + nch);
+    LBM_CUDA(launch_classify_count(S.mask, c->n_store, wide ? 1 : 0, cls_d, c->stream), "classify slots");
+    std::vector<int4> cls(nch);
     uint32_t errv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     LBM_CUDA(cudaMemcpyAsync(errv, errw, 32, cudaMemcpyDeviceToHost, c->stream), "copy error words");
-    std::vector<uint32_t> hmask(c->n_store);
-    if (c->n_store > 0)
-        LBM_CUDA(cudaMemcpyAsync(hmask.data(), S.mask, (size_t)c->n_store * 4, cudaMemcpyDeviceToHost, c->stream),
-                 "copy masks");
+    if (nch > 0)
+        LBM_CUDA(cudaMemcpyAsync(cls.data(), cls_d, (size_t)nch * sizeof(int4), cudaMemcpyDeviceToHost, c->stream),
+                 "copy slot classes");
     LBM_CUDA(cudaStreamSynchronize(c->stream), "setup sync");
     if (errv[0]) {
         float bad_phi;
@@ -463,30 +471,37 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     }
     // host tables: ghost count, outlet slots, general list (the dense index of
     // every slot is built on the first call that scatters to host memory)
-    const bool wide = (unsigned long long)grid->q * (unsigned long long)c->n_store >= (1ull << 32);
     c->host_idx.clear();
-    c->out_slots.clear();
-    c->general.clear();
     c->n_ghost = 0;
     c->n_in = 0;
-    for (int p = 0; p < c->n_store; ++p) {
-        const uint32_t m = hmask[p];
-        if (!(m & (kGhostBit | kGeneralBits)) && !wide) continue;
-        if (m & kGhostBit) {
-            ++c->n_ghost;
-            continue;
-        }
-        const uint32_t type = (m >> kTypeShift) & 3u;
-        if (type == kOutlet) c->out_slots.push_back((uint32_t)p);
-        if (type == kInlet) ++c->n_in;
-        c->general.push_back((uint32_t)p);
+    std::vector<int2> off(nch);
+    int ngen = 0, nout = 0;
+    for (int k = 0; k < nch; ++k) {
+        off[k] = make_int2(ngen, nout);
+        ngen += cls[k].x;
+        nout += cls[k].y;
+        c->n_ghost += cls[k].z;
+        c->n_in += cls[k].w;
+    }
+    c->general.assign((size_t)ngen, 0u);
+    c->out_slots.assign((size_t)nout, 0u);
+    if (nch > 0 && (ngen > 0 || nout > 0)) {
+        LBM_CUDA(cudaMemcpyAsync(off_d, off.data(), (size_t)nch * sizeof(int2), cudaMemcpyHostToDevice, c->stream),
+                 "copy class offsets");
+        LBM_CUDA(launch_classify_write(S.mask, c->n_store, wide ? 1 : 0, off_d, c->at<uint32_t>(c->L.general),
+                                       outl_d, c->stream),
+                 "list general and outlet slots");
+        if (ngen > 0)
+            LBM_CUDA(cudaMemcpyAsync(c->general.data(), c->at<uint32_t>(c->L.general), (size_t)ngen * 4,
+                                     cudaMemcpyDeviceToHost, c->stream), "copy general list");
+        if (nout > 0)
+            LBM_CUDA(cudaMemcpyAsync(c->out_slots.data(), outl_d, (size_t)nout * 4, cudaMemcpyDeviceToHost,
+                                     c->stream), "copy outlet list");
+        LBM_CUDA(cudaStreamSynchronize(c->stream), "slot lists sync");
     }
     c->n_out = (int)c->out_slots.size();
     c->all_general = c->general;
     c->halo_masks.clear();
-    if (!c->general.empty())
-        LBM_CUDA(cudaMemcpyAsync(c->at<uint32_t>(c->L.general), c->general.data(), c->general.size() * 4,
-                                 cudaMemcpyHostToDevice, c->stream), "copy general list");
 
     // Lattice units from the Table 1 scales (Sec. 4): nu = mu / rho0 * dt / dx^2.
     const double scale = rheo->dt / (rheo->dx * rheo->dx);

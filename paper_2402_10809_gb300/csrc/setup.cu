@@ -269,6 +269,93 @@ __global__ void fill_u32(uint32_t* p, long long n, uint32_t v)
     if (i < n) p[i] = v;
 }
 
+// Slot classes of the host tables, in chunks of kClassChunk slots (each of
+// the kClassBlock threads takes kClassPer consecutive slots): general-path
+// cells (inlet, outlet, periodic wrap; every cell when wide), outlet cells,
+// ghost slots, inlet cells.
+constexpr int kClassBlock = 256, kClassPer = 4, kClassChunk = kClassBlock * kClassPer;
+
+__device__ __forceinline__ void slot_classes(const uint32_t* __restrict__ mask, int n, int wide, int first, int& gen,
+                                             int& out, int& ghost, int& inl)
+{
+    gen = out = ghost = inl = 0;
+    for (int k = 0; k < kClassPer; ++k) {
+        const int p = first + k;
+        if (p >= n) break;
+        const uint32_t m = mask[p];
+        if (m & kGhostBit) {
+            ++ghost;
+            continue;
+        }
+        const uint32_t type = (m >> kTypeShift) & 3u;
+        gen += (wide || (m & kGeneralBits)) ? 1 : 0;
+        out += type == kOutlet;
+        inl += type == kInlet;
+    }
+}
+
+// Exclusive scan over the block of v (ordered by thread), and the block total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* total)
+{
+    __shared__ int warp_sum[kClassBlock / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[wid] = x;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < kClassBlock / 32; ++w) {
+        before += w < wid ? warp_sum[w] : 0;
+        all += warp_sum[w];
+    }
+    *total = all;
+    return before + x - v;
+}
+
+// Per chunk: counts of general, outlet, ghost and inlet slots.
+__global__ void __launch_bounds__(kClassBlock) classify_count(const uint32_t* __restrict__ mask, int n, int wide,
+                                                              int4* __restrict__ counts)
+{
+    int g, o, h, i;
+    slot_classes(mask, n, wide, blockIdx.x * kClassChunk + threadIdx.x * kClassPer, g, o, h, i);
+    int tg, to, th, ti;
+    block_exclusive_scan(g, &tg);
+    __syncthreads();
+    block_exclusive_scan(o, &to);
+    __syncthreads();
+    block_exclusive_scan(h, &th);
+    __syncthreads();
+    block_exclusive_scan(i, &ti);
+    if (threadIdx.x == 0) counts[blockIdx.x] = make_int4(tg, to, th, ti);
+}
+
+// The general and outlet slots in ascending order, chunk c starting at
+// offsets[c] (x: general list, y: outlet list).
+__global__ void __launch_bounds__(kClassBlock) classify_write(const uint32_t* __restrict__ mask, int n, int wide,
+                                                              const int2* __restrict__ offsets,
+                                                              uint32_t* __restrict__ general,
+                                                              uint32_t* __restrict__ outlets)
+{
+    const int first = blockIdx.x * kClassChunk + threadIdx.x * kClassPer;
+    int g, o, h, i, tot;
+    slot_classes(mask, n, wide, first, g, o, h, i);
+    int pg = offsets[blockIdx.x].x + block_exclusive_scan(g, &tot);
+    __syncthreads();
+    int po = offsets[blockIdx.x].y + block_exclusive_scan(o, &tot);
+    for (int k = 0; k < kClassPer; ++k) {
+        const int p = first + k;
+        if (p >= n) break;
+        const uint32_t m = mask[p];
+        if (m & kGhostBit) continue;
+        if (wide || (m & kGeneralBits)) general[pg++] = (uint32_t)p;
+        if (((m >> kTypeShift) & 3u) == kOutlet) outlets[po++] = (uint32_t)p;
+    }
+}
+
 // Number of non-ghost slots whose region byte (dense) is set; with wall_bits
 // nonzero only plain fluid cells with a wall link (mask & wall_bits) count.
 __global__ void region_count(const uint32_t* __restrict__ rows, const int* __restrict__ rowbase,
@@ -362,6 +449,23 @@ cudaError_t launch_fill_u32(uint32_t* p, long long n, uint32_t v, cudaStream_t s
 {
     if (n == 0) return cudaSuccess;
     fill_u32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+int classify_chunks(int n) { return (n + kClassChunk - 1) / kClassChunk; }
+
+cudaError_t launch_classify_count(const uint32_t* mask, int n, int wide, int4* counts, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    classify_count<<<classify_chunks(n), kClassBlock, 0, s>>>(mask, n, wide, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify_write(const uint32_t* mask, int n, int wide, const int2* offsets, uint32_t* general,
+                                  uint32_t* outlets, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    classify_write<<<classify_chunks(n), kClassBlock, 0, s>>>(mask, n, wide, offsets, general, outlets);
     return cudaGetLastError();
 }
 

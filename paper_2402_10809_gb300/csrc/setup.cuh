@@ -46,6 +46,13 @@ cudaError_t launch_setup_mask(int q, const SetupParams& S, cudaStream_t s);
 cudaError_t launch_diag_finish(const double* partials, int nblk, double* out, cudaStream_t s);
 cudaError_t launch_fill_f32(float* p, long long n, float v, cudaStream_t s);
 cudaError_t launch_fill_u32(uint32_t* p, long long n, uint32_t v, cudaStream_t s);
+// Host tables of a layout: classify_count gives each chunk of slots its
+// counts (general, outlet, ghost, inlet); classify_write, from the chunks'
+// exclusive offsets (general, outlet), the ascending general and outlet lists.
+int classify_chunks(int n);
+cudaError_t launch_classify_count(const uint32_t* mask, int n, int wide, int4* counts, cudaStream_t s);
+cudaError_t launch_classify_write(const uint32_t* mask, int n, int wide, const int2* offsets, uint32_t* general,
+                                  uint32_t* outlets, cudaStream_t s);
 cudaError_t launch_region_count(const uint32_t* rows, const int* rowbase, const uint32_t* mask, int n_store, int nx,
                                 const uint8_t* region, uint32_t wall_bits, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_scatter_f64(const uint32_t* rows, const int* rowbase, const uint32_t* mask, int n_store, int nx,
