@@ -560,7 +560,7 @@ def coil_study(torch, lbm, args):
         timed_steps = (steps // every - 1) * every
         n_fluid = sim.n_fluid
         sim.close()
-        return {"fluid_cells": int(n_fluid), "value": float(n_fluid * timed_steps / t_run / 1e6), "unit": UNIT,
+        return {"fluid_cells": int(n_fluid), "value": float(n_fluid * timed_steps / t_run / 1e6) if t_run > 0 else None, "unit": UNIT,
                 "sac_mean_u": float(u_sum / max(k, 1)), "sac_volume_mean_u": float(v_sum / max(k, 1)),
                 "sac_wall_mean_wss": float(w_sum / max(k, 1)), "sac_wall_cells": int(wall.sum().item()),
                 "finite": bool(bad == 0)}

@@ -2,7 +2,10 @@
 porosity (oracle/porosity.py).  The count is exact integer work and the
 quotient is correctly rounded on both sides, so the comparison is bit-exact.
 
-Cases: odd and even windows up to 40 cells, a window wider than the box,
+Cases: odd and even windows up to 40 cells (the y and z passes keep the
+trailing edge of their running sums in a shared-memory ring) and of 60 and
+100 cells (the passes that would need a ring over 48 KB re-read it instead),
+a window wider than the box,
 window 1 (the wire itself), ragged x extents (scalar path), segments along y
 and z that end mid-way, unaligned output (scalar path), solid override; the
 512^3 box of the coil study at the paper's 28-cell window on sampled cells;
@@ -47,6 +50,8 @@ CASES = [
     ((96, 70, 300), 32, 0.05, 0.02, True),   # long z: several running-sum segments per line
     ((70, 45, 60), 40, 0.05, 0.3, True),
     ((68, 40, 33), 33, 0.0, 0.1, False),
+    ((40, 36, 70), 60, 0.05, 0.3, True),     # z pass without the ring (its ring would exceed 48 KB)
+    ((44, 30, 20), 100, 0.0, 0.3, False),    # neither pass with the ring
 ]
 
 
