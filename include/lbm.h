@@ -313,9 +313,15 @@ lbm_status lbm_porosity_average(int32_t nx, int32_t ny, int32_t nz, const uint8_
  *  - lbm_set_l2_window: max_bytes < 0 the default (a quarter of the L2),
  *    0 no window, > 0 at most that many bytes.  Results are identical either
  *    way.
- *  - lbm_l2_window_bytes: the window in bytes (0 none; -1 bad context). */
+ *  - lbm_l2_window_bytes: the window in bytes (0 none; -1 bad context).
+ *  - lbm_set_l2_group: contexts given the same nonzero group (the z-slabs of
+ *    one problem stepping in turn on one device) take the persisting L2 over
+ *    from each other without returning the other's lines to normal; their
+ *    windows should fit the L2's persisting part together.  0 (the default)
+ *    leaves a context on its own. */
 lbm_status lbm_set_l2_window(lbm_ctx* ctx, int64_t max_bytes);
 int64_t lbm_l2_window_bytes(const lbm_ctx* ctx);
+lbm_status lbm_set_l2_group(lbm_ctx* ctx, int64_t group);
 
 /* Every check_every steps of later lbm_step calls, run the non-finite count of
  * lbm_diag and return LBM_EUNSTABLE when it is nonzero (0 = never, default). */

@@ -162,6 +162,7 @@ struct lbm_ctx {
     int halo_lo = 0, halo_hi = 0;     // halo planes of a z-slab (lbm_set_halo)
     std::vector<uint32_t> halo_masks;    // the masks the halo planes had before they became halos
     std::vector<uint32_t> all_general;   // the general list without halo planes removed
+    long long l2_group = 0;           // contexts of one nonzero group share the persisting L2 without resets
     std::string err;
 
     template <class T>
@@ -245,6 +246,13 @@ static cudaError_t l2_claim(const lbm_ctx* c)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kL2Devices) return e;
     if (g_l2_owner[dev] == c) return cudaSuccess;
+    const lbm_ctx* o = g_l2_owner[dev];
+    if (o && c->l2_group != 0 && o->l2_group == c->l2_group) {
+        // the slabs of one problem: their windows together stay within the
+        // persisting limit, so the lines of the others may stay
+        g_l2_owner[dev] = c;
+        return cudaSuccess;
+    }
     e = cudaCtxResetPersistingL2Cache();
     if (e == cudaSuccess) g_l2_owner[dev] = c;
     return e;
@@ -771,6 +779,14 @@ extern "C" lbm_status lbm_set_l2_window(lbm_ctx* c, int64_t max_bytes)
 }
 
 extern "C" int64_t lbm_l2_window_bytes(const lbm_ctx* c) { return c && c->ready ? (int64_t)c->base.l2_bytes : -1; }
+
+extern "C" lbm_status lbm_set_l2_group(lbm_ctx* c, int64_t group)
+{
+    if (!c) return LBM_EINVAL;
+    if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    c->l2_group = group;
+    return LBM_OK;
+}
 
 extern "C" lbm_status lbm_set_check(lbm_ctx* c, int32_t check_every)
 {

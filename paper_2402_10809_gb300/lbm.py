@@ -26,7 +26,7 @@ SYMBOLS = ["lbm_list_length", "lbm_workspace_size", "lbm_init", "lbm_step", "lbm
            "lbm_porosity_workspace_size", "lbm_porosity_average", "lbm_anisotropy_buffer_size",
            "lbm_set_anisotropy", "lbm_slab_bounds", "lbm_plane_slots", "lbm_set_halo", "lbm_halo_message_size",
            "lbm_halo_pack", "lbm_halo_unpack", "lbm_halo_exchange", "lbm_set_l2_window",
-           "lbm_l2_window_bytes"]
+           "lbm_l2_window_bytes", "lbm_set_l2_group"]
 
 
 class lbm_grid(C.Structure):
@@ -138,6 +138,8 @@ def load(build_if_missing=True):
     L.lbm_set_l2_window.argtypes = [vp, C.c_int64]
     L.lbm_l2_window_bytes.restype = C.c_int64
     L.lbm_l2_window_bytes.argtypes = [vp]
+    L.lbm_set_l2_group.restype = C.c_int
+    L.lbm_set_l2_group.argtypes = [vp, C.c_int64]
     L.lbm_destroy.restype = None
     L.lbm_destroy.argtypes = [vp]
     _lib = L
@@ -234,6 +236,10 @@ def lbm_set_l2_window(ctx, max_bytes=-1):
 
 def lbm_l2_window_bytes(ctx):
     return int(load().lbm_l2_window_bytes(ctx))
+
+
+def lbm_set_l2_group(ctx, group):
+    _check(ctx, load().lbm_set_l2_group(ctx, int(group)))
 
 
 def lbm_set_check(ctx, check_every):

@@ -69,6 +69,9 @@ class SlabSimulation:
             sub, h0, h1 = slab_problem(problem, self.bounds[k], self.bounds[k + 1])
             sim = L.Simulation(sub, storage=storage, device=device, stream=self.stream)
             L.lbm_set_halo(sim.ctx, h0, h1)
+            # the slabs step in turn: they share the persisting L2 (their
+            # per-slot words together are the unsharded box's)
+            L.lbm_set_l2_group(sim.ctx, id(self))
             self.sims.append(sim)
             self.halo.append((h0, h1))
 
