@@ -270,6 +270,18 @@ lbm_status lbm_halo_pack(lbm_ctx* ctx, int32_t side, void* dst);
 lbm_status lbm_halo_unpack(lbm_ctx* ctx, int32_t side, const void* src);
 lbm_status lbm_halo_exchange(lbm_ctx* lower, lbm_ctx* upper);
 
+/* lbm_step_slabs: `steps` time steps of the n adjacent z-slabs slabs[0..n-1]
+ * (bottom to top) of one problem on one device, each slab on its own
+ * context's stream (the streams may differ or coincide): every slab's step
+ * waits only for the exchanges of its own faces, and each face's exchange
+ * (as lbm_halo_exchange, launched on the lower slab's stream) only for the
+ * steps of its two slabs, so slabs step concurrently.  join_stream (NULL:
+ * the default stream) orders the whole run after its earlier work and its
+ * later work after the run.  The same results as lbm_step of every slab followed by
+ * lbm_halo_exchange of every face, step by step.  Returns the first error;
+ * LBM_EINVAL for slabs that are not adjacent slabs of one lattice. */
+lbm_status lbm_step_slabs(lbm_ctx** slabs, int32_t n, int32_t steps, void* join_stream);
+
 /* Volume-averaged porosity of a voxelised coil, the input that lbm_init takes
  * as the porosity of the averaged simulations (Sec. 4: the porosity field is
  * the windowed convolution of the voxelised coil with a uniform averaging

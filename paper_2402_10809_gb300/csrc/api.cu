@@ -1300,6 +1300,8 @@ extern "C" lbm_status lbm_halo_unpack(lbm_ctx* c, int32_t side, const void* src)
     return halo_pack_unpack(c, side, nullptr, src, false);
 }
 
+static lbm_status halo_exchange_on(lbm_ctx* lower, lbm_ctx* upper, cudaStream_t s);
+
 extern "C" lbm_status lbm_halo_exchange(lbm_ctx* lower, lbm_ctx* upper)
 {
     if (!lower || !upper || lower == upper) return LBM_EINVAL;
@@ -1310,6 +1312,13 @@ extern "C" lbm_status lbm_halo_exchange(lbm_ctx* lower, lbm_ctx* upper)
         lower->grid.nx != upper->grid.nx || lower->grid.ny != upper->grid.ny)
         return fail(lower, LBM_EINVAL, "slabs of different lattices, storage types or x-y extents");
     if (lower->stream != upper->stream) return fail(lower, LBM_EINVAL, "the two slabs must share one stream");
+    return halo_exchange_on(lower, upper, lower->stream);
+}
+
+// The copies of lbm_halo_exchange, launched on stream s (the caller orders
+// them after both slabs' steps).
+static lbm_status halo_exchange_on(lbm_ctx* lower, lbm_ctx* upper, cudaStream_t s)
+{
     const FaceSpec fl = face_of(lower, 1), fu = face_of(upper, 0);
     const long long a = lower->plane_first[fl.send_plane + 1] - lower->plane_first[fl.send_plane];
     const long long b = upper->plane_first[fu.recv_plane + 1] - upper->plane_first[fu.recv_plane];
@@ -1335,8 +1344,83 @@ extern "C" lbm_status lbm_halo_exchange(lbm_ctx* lower, lbm_ctx* upper)
         H.dst[H.ntask] = sl + ((size_t)dn[k] * nl + (size_t)lower->plane_first[fl.recv_plane]) * es;
         H.count[H.ntask++] = c2;
     }
-    const cudaError_t e = launch_halo_copy(H, lower->stream);
+    const cudaError_t e = launch_halo_copy(H, s);
     return e == cudaSuccess ? LBM_OK : cuda_fail(lower, e, "halo exchange");
+}
+
+extern "C" lbm_status lbm_step_slabs(lbm_ctx** slabs, int32_t n, int32_t steps, void* join_stream)
+{
+    if (!slabs || n < 1 || steps < 0) return LBM_EINVAL;
+    for (int k = 0; k < n; ++k) {
+        if (!slabs[k]) return LBM_EINVAL;
+        if (!slabs[k]->ready) return fail(slabs[k], LBM_ESTATE, "context not initialised");
+    }
+    for (int k = 0; k + 1 < n; ++k) {
+        lbm_ctx* lo = slabs[k];
+        lbm_ctx* up = slabs[k + 1];
+        if (!lo->halo_hi || !up->halo_lo)
+            return fail(lo, LBM_EINVAL, "the lower slab needs an upper halo plane and the upper slab a lower one");
+        if (lo->grid.q != up->grid.q || lo->grid.storage != up->grid.storage || lo->grid.nx != up->grid.nx ||
+            lo->grid.ny != up->grid.ny)
+            return fail(lo, LBM_EINVAL, "slabs of different lattices, storage types or x-y extents");
+    }
+    if (steps == 0) return LBM_OK;
+    lbm_ctx* c = slabs[0];  // errors of the events go to the first slab
+    std::vector<cudaEvent_t> ev((size_t)2 * n + 1, nullptr);
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    for (cudaEvent_t& e : ev) {
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cleanup();
+            return fail(c, LBM_ECUDA, "event creation");
+        }
+    }
+    cudaEvent_t* step_done = ev.data();        // [n]
+    cudaEvent_t* exch_done = ev.data() + n;    // [n - 1] face k | k + 1
+    cudaEvent_t start = ev[(size_t)2 * n];
+    const cudaStream_t join = static_cast<cudaStream_t>(join_stream);
+    lbm_status st = LBM_OK;
+    auto check = [&](cudaError_t e, const char* where) {
+        if (e != cudaSuccess && st == LBM_OK) st = cuda_fail(c, e, where);
+        return st == LBM_OK;
+    };
+    // join_stream may be the legacy default stream (NULL): always join
+    check(cudaEventRecord(start, join), "join");
+    for (int k = 0; k < n && st == LBM_OK; ++k) check(cudaStreamWaitEvent(slabs[k]->stream, start, 0), "join");
+    for (int t = 0; t < steps && st == LBM_OK; ++t) {
+        // every slab steps on its own stream once the faces of the last
+        // exchange that touched it are done
+        for (int k = 0; k < n && st == LBM_OK; ++k) {
+            if (t > 0 && k > 0 && !check(cudaStreamWaitEvent(slabs[k]->stream, exch_done[k - 1], 0), "wait")) break;
+            if (t > 0 && k + 1 < n && !check(cudaStreamWaitEvent(slabs[k]->stream, exch_done[k], 0), "wait")) break;
+            const lbm_status s1 = lbm_step(slabs[k], 1);
+            if (s1 != LBM_OK) {
+                if (slabs[k] != c) c->err = slabs[k]->err;
+                st = s1;
+                break;
+            }
+            check(cudaEventRecord(step_done[k], slabs[k]->stream), "record");
+        }
+        // then each face, on the lower slab's stream, after the upper slab's step
+        for (int k = 0; k + 1 < n && st == LBM_OK; ++k) {
+            if (!check(cudaStreamWaitEvent(slabs[k]->stream, step_done[k + 1], 0), "wait")) break;
+            const lbm_status s2 = halo_exchange_on(slabs[k], slabs[k + 1], slabs[k]->stream);
+            if (s2 != LBM_OK) {
+                if (slabs[k] != c) c->err = slabs[k]->err;
+                st = s2;
+                break;
+            }
+            check(cudaEventRecord(exch_done[k], slabs[k]->stream), "record");
+        }
+    }
+    for (int k = 0; k < n; ++k) {
+        // the slabs' last work, whatever happened above, before the join stream's next
+        if (cudaEventRecord(step_done[k], slabs[k]->stream) == cudaSuccess) cudaStreamWaitEvent(join, step_done[k], 0);
+    }
+    cleanup();
+    return st;
 }
 
 // ---------------------------------------------------------------------------

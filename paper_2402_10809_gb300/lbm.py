@@ -26,7 +26,7 @@ SYMBOLS = ["lbm_list_length", "lbm_workspace_size", "lbm_init", "lbm_step", "lbm
            "lbm_porosity_workspace_size", "lbm_porosity_average", "lbm_anisotropy_buffer_size",
            "lbm_set_anisotropy", "lbm_slab_bounds", "lbm_plane_slots", "lbm_set_halo", "lbm_halo_message_size",
            "lbm_halo_pack", "lbm_halo_unpack", "lbm_halo_exchange", "lbm_set_l2_window",
-           "lbm_l2_window_bytes", "lbm_set_l2_group"]
+           "lbm_l2_window_bytes", "lbm_set_l2_group", "lbm_step_slabs"]
 
 
 class lbm_grid(C.Structure):
@@ -140,6 +140,8 @@ def load(build_if_missing=True):
     L.lbm_l2_window_bytes.argtypes = [vp]
     L.lbm_set_l2_group.restype = C.c_int
     L.lbm_set_l2_group.argtypes = [vp, C.c_int64]
+    L.lbm_step_slabs.restype = C.c_int
+    L.lbm_step_slabs.argtypes = [C.POINTER(vp), C.c_int32, C.c_int32, vp]
     L.lbm_destroy.restype = None
     L.lbm_destroy.argtypes = [vp]
     _lib = L
@@ -240,6 +242,14 @@ def lbm_l2_window_bytes(ctx):
 
 def lbm_set_l2_group(ctx, group):
     _check(ctx, load().lbm_set_l2_group(ctx, int(group)))
+
+
+def lbm_step_slabs(ctxs, steps, join_stream=None):
+    """Time steps of adjacent z-slab contexts (bottom to top), each on its
+    own stream, faces exchanged as they become ready; ordered against
+    join_stream (None or 0: the default stream)."""
+    arr = (C.c_void_p * len(ctxs))(*ctxs)
+    _check(ctxs[0], load().lbm_step_slabs(arr, len(ctxs), int(steps), join_stream))
 
 
 def lbm_set_check(ctx, check_every):

@@ -56,18 +56,27 @@ def combine_diag(parts):
 
 
 class SlabSimulation:
-    """One problem as ``nslabs`` z-slabs on one device (one stream)."""
+    """One problem as ``nslabs`` z-slabs on one device.  With ``concurrent``
+    every slab has a stream of its own and lbm_step_slabs lets the slabs step
+    at the same time (each face exchanged once its two slabs have stepped);
+    otherwise all of them share the current stream and step in turn.  Either
+    way the work is ordered against the current stream of the device."""
 
-    def __init__(self, problem, nslabs, storage="f32", device="cuda"):
+    def __init__(self, problem, nslabs, storage="f32", device="cuda", concurrent=True):
         import torch
 
         self.problem = problem
         self.bounds = slab_bounds(problem, nslabs)
-        self.stream = torch.cuda.current_stream(torch.device(device))
+        dev = torch.device(device)
+        self.stream = torch.cuda.current_stream(dev)
+        self.streams = [torch.cuda.Stream(dev) if concurrent else self.stream for _ in range(nslabs)]
         self.sims, self.halo = [], []
         for k in range(nslabs):
             sub, h0, h1 = slab_problem(problem, self.bounds[k], self.bounds[k + 1])
-            sim = L.Simulation(sub, storage=storage, device=device, stream=self.stream)
+            if concurrent:
+                # the set-up on the slab's stream follows the current stream's work
+                self.streams[k].wait_stream(self.stream)
+            sim = L.Simulation(sub, storage=storage, device=device, stream=self.streams[k])
             L.lbm_set_halo(sim.ctx, h0, h1)
             # the slabs step in turn: they share the persisting L2 (their
             # per-slot words together are the unsharded box's)
@@ -76,6 +85,8 @@ class SlabSimulation:
             self.halo.append((h0, h1))
 
     def close(self):
+        for st in self.streams:
+            st.synchronize()  # before the workspaces go back to the allocator
         for s in self.sims:
             s.close()
 
@@ -84,11 +95,7 @@ class SlabSimulation:
         return self.sims[0].t
 
     def step(self, n=1):
-        for _ in range(n):
-            for s in self.sims:
-                L.lbm_step(s.ctx, 1)
-            for k in range(len(self.sims) - 1):
-                L.lbm_halo_exchange(self.sims[k].ctx, self.sims[k + 1].ctx)
+        L.lbm_step_slabs([s.ctx for s in self.sims], n, self.stream.cuda_stream)
 
     def moments(self):
         """rho, u, gdot, omega on the dense box (host), from the slabs' interiors."""

@@ -40,8 +40,8 @@ def test_packed_messages_equal_the_direct_exchange(lbm):
     from paper_2402_10809_gb300 import slabs
 
     prob = aneurysm_problem(48, q=19, u0=0.05, period=100.0)
-    direct = slabs.SlabSimulation(prob, 2)
-    packed = slabs.SlabSimulation(prob, 2)
+    direct = slabs.SlabSimulation(prob, 2)  # concurrent slabs, lbm_step_slabs
+    packed = slabs.SlabSimulation(prob, 2, concurrent=False)  # one stream, stepped by hand
     lo, hi = packed.sims
     n_up = lbm.lbm_halo_message_size(lo.ctx, 1)
     n_dn = lbm.lbm_halo_message_size(hi.ctx, 0)
@@ -81,6 +81,10 @@ def test_halo_arguments_are_checked(lbm):
     lbm.lbm_set_halo(other.ctx, 1, 0)
     with pytest.raises(lbm.LBMError):
         lbm.lbm_halo_exchange(s.ctx, other.ctx)  # different lattices
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_step_slabs([s.ctx, other.ctx], 1)
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_step_slabs([other.ctx, s.ctx], 1)  # not bottom to top
     s.close()
     other.close()
 
