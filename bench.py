@@ -314,6 +314,7 @@ def run_ours(args):
     if rank == 0 and not args.no_slabs:
         line["slabs_one_gpu"] = slab_overhead(torch, lbm, prob, args, flush, mlups / ws)
     if rank == 0 and not args.no_config2:
+        line["config1"] = config1_throughput(torch, lbm, args, flush)
         line["config2"] = config2_throughput(torch, lbm, args, flush)
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = adjoint_cost(torch, lbm, args, args.adjoint_n)
@@ -644,7 +645,32 @@ def cpu_baseline(prob, sim_factory=None, sample_steps=30, error_steps=1000):
                         "after_steps": steps}
             s.close()
         out["error_vs_oracle"] = errs
+        out["error_vs_oracle_pipe"] = pipe_error()
     return out
+
+
+def pipe_error(steps=200):
+    """The 32x32x64 D3Q19 pipe (Carreau-Yasuda, porous plug, body force,
+    periodic in z) after its 200 steps on the GPU (FP32 storage) against the
+    oracle: largest velocity and shear-rate deviation over the fluid cells
+    relative to the oracle's largest value."""
+    from lbm_inputs import pipe_problem
+    from oracle.oracle import Oracle
+    from paper_2402_10809_gb300 import lbm
+
+    prob = pipe_problem(q=19)
+    o = Oracle(prob)
+    o.step(steps)
+    r = o.moments()
+    o.close()
+    s = lbm.Simulation(prob, storage="f32")
+    s.step(steps)
+    g = s.moments()
+    s.close()
+    fl = prob.flags > 0
+    return {"workload": f"pipe 32x32x64 D3Q19 f32-stored, {steps} steps",
+            "u_max_rel": float(np.abs(g["u"][:, fl] - r["u"][:, fl]).max() / np.abs(r["u"][:, fl]).max()),
+            "gdot_max_rel": float(np.abs(g["gdot"][fl] - r["gdot"][fl]).max() / np.abs(r["gdot"][fl]).max())}
 
 
 def slab_overhead(torch, lbm, prob, args, flush, unsharded):
@@ -675,6 +701,23 @@ def slab_overhead(torch, lbm, prob, args, flush, unsharded):
         res[f"slabs{ns}"] = {"value": v, "unit": UNIT, "vs_unsharded": v / unsharded, "bounds": sl.bounds,
                              "finite": finite}
     return res
+
+
+def config1_throughput(torch, lbm, args, flush):
+    """The 32x32x64 D3Q19 pipe (FP32) over its 200 time steps as one timed
+    run after a warm-up run, L2 flushed before each; a box this small is
+    bound by the launches, not by HBM."""
+    from lbm_inputs import pipe_problem
+
+    prob = pipe_problem(q=19)
+    L = 200
+    sim, tv = time_variant(torch, lbm, prob, "f32", 3, 1, L, flush)
+    finite = bool(sim.diag()[7] == 0)
+    sim.close()
+    t = min(tv)
+    return {"workload": f"pipe 32x32x64 D3Q19 f32-stored, {L} time steps, {prob.n_fluid} fluid cells",
+            "value": prob.n_fluid * L / t / 1e6, "unit": UNIT, "seconds": t, "us_per_step": 1e6 * t / L,
+            "finite": finite}
 
 
 def config2_throughput(torch, lbm, args, flush):
@@ -740,7 +783,7 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=30)
     ap.add_argument("--error-steps", type=int, default=WORKLOAD["lbm_steps"],
                     help="time steps after which every storage type is compared with the oracle")
-    ap.add_argument("--no-config2", action="store_true", help="skip the 256^3, 2000-step throughput")
+    ap.add_argument("--no-config2", action="store_true", help="skip the pipe (200 steps) and 256^3 (2000 steps) throughputs")
     ap.add_argument("--no-slabs", action="store_true", help="skip the z-slab split on one GPU")
     ap.add_argument("--adjoint-n2", type=int, default=256, help="second adjoint box (0: none)")
     ap.add_argument("--ref-sample-steps", type=int, default=4)
