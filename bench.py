@@ -46,11 +46,11 @@ def bytes_per_update(q, storage):
 
 
 def kernel_source_hash():
-    """Hash of the sources the step kernel is compiled from (a stored traffic
-    figure is only reported while they are unchanged)."""
+    """Hash of the sources and build flags the step kernel is compiled from (a
+    stored traffic figure is only reported while they are unchanged)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2402_10809_gb300", "csrc")
-    for fn in ("kernels.cuh", "lattice.cuh", "step.cu"):
+    for fn in ("kernels.cuh", "lattice.cuh", "step.cu", os.path.join("..", "build.py")):
         with open(os.path.join(csrc, fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
