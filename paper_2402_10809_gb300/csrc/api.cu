@@ -3,6 +3,7 @@
 // fused step, moments and diagnostics kernels.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -163,6 +164,14 @@ struct lbm_ctx {
     std::vector<uint32_t> halo_masks;    // the masks the halo planes had before they became halos
     std::vector<uint32_t> all_general;   // the general list without halo planes removed
     long long l2_group = 0;           // contexts of one nonzero group share the persisting L2 without resets
+    // CUDA graphs of kGraphSteps time steps (problems without a velocity
+    // inlet, whose steps do not depend on the time), one per starting buffer,
+    // valid while params_gen is the generation they were captured at
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    unsigned long long graph_gen[2] = {0, 0};
+    unsigned long long params_gen = 1;
+    cudaStream_t capture_stream = nullptr;
+    bool graphs_ok = true;
     std::string err;
 
     template <class T>
@@ -196,6 +205,7 @@ static lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where)
 // Devices without persisting L2 get no window.
 static cudaError_t l2_window(lbm_ctx* c, long long cap)
 {
+    ++c->params_gen;
     Params& P = c->base;
     P.l2_base = nullptr;
     P.l2_bytes = 0;
@@ -580,21 +590,87 @@ extern "C" lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const uint8_
     return LBM_OK;
 }
 
+// Time steps per captured graph (even: the state ends in the buffer it
+// started from).
+constexpr int kGraphSteps = 32;
+
+// The graph of kGraphSteps time steps from the current buffer, captured on a
+// private stream (capture does not run anything) the first time it is needed
+// and again after any change of the step's parameters.  Without a velocity
+// inlet no kernel reads the time, so one graph serves every later run.
+// nullptr if capture or instantiation fails (the caller launches steps one
+// by one from then on).
+static cudaGraphExec_t step_graph(lbm_ctx* c)
+{
+    const int k = c->cur;
+    if (c->graph[k] && c->graph_gen[k] == c->params_gen) return c->graph[k];
+    if (c->graph[k]) {
+        cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+    }
+    if (!c->capture_stream && cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        c->graphs_ok = false;
+        return nullptr;
+    }
+    if (cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        (void)cudaGetLastError();
+        c->graphs_ok = false;
+        return nullptr;
+    }
+    bool ok = true;
+    int cur = k;
+    for (int s = 0; s < kGraphSteps && ok; ++s) {
+        Params P = c->base;
+        P.fsrc = c->f(cur);
+        P.fdst = c->f(1 - cur);
+        P.t = 0;  // not read: no velocity inlet
+        ok = launch(c->grid, kModeStep, P, c->capture_stream) == cudaSuccess;
+        cur ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->capture_stream, &g);
+    cudaGraphExec_t x = nullptr;
+    if (ok && e == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
+        c->graph[k] = x;
+        c->graph_gen[k] = c->params_gen;
+    } else {
+        (void)cudaGetLastError();
+        c->graphs_ok = false;
+    }
+    if (g) cudaGraphDestroy(g);
+    return c->graph[k];
+}
+
 extern "C" lbm_status lbm_step(lbm_ctx* c, int32_t n)
 {
     if (!c) return LBM_EINVAL;
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
     if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
     if (n > 0) LBM_CUDA(l2_claim(c), "claim the persisting L2");
-    for (int32_t s = 0; s < n; ++s) {
-        Params P = c->base;
-        P.fsrc = c->f(c->cur);
-        P.fdst = c->f(1 - c->cur);
-        P.t = c->t;
-        LBM_CUDA(launch(c->grid, kModeStep, P, c->stream), "step kernel");
-        c->cur ^= 1;
-        c->t += 1;
-        if (c->check_every > 0 && ++c->since_check >= c->check_every) {
+    // problems without a velocity inlet run whole graphs of steps where the
+    // steps up to the next instability check allow
+    const bool graphs = c->graphs_ok && c->bc.inlet_axis < 0;
+    for (int32_t s = 0; s < n;) {
+        const long long to_check = c->check_every > 0 ? c->check_every - c->since_check : LLONG_MAX;
+        cudaGraphExec_t x = (graphs && n - s >= kGraphSteps && to_check >= kGraphSteps) ? step_graph(c) : nullptr;
+        if (x) {
+            LBM_CUDA(cudaGraphLaunch(x, c->stream), "step graph");
+            c->t += kGraphSteps;
+            s += kGraphSteps;
+            if (c->check_every > 0) c->since_check += kGraphSteps;
+        } else {
+            Params P = c->base;
+            P.fsrc = c->f(c->cur);
+            P.fdst = c->f(1 - c->cur);
+            P.t = c->t;
+            LBM_CUDA(launch(c->grid, kModeStep, P, c->stream), "step kernel");
+            c->cur ^= 1;
+            c->t += 1;
+            s += 1;
+            if (c->check_every > 0) c->since_check += 1;
+        }
+        if (c->check_every > 0 && c->since_check >= c->check_every) {
             c->since_check = 0;
             double d[8];
             lbm_status st = run_diag(c, nullptr, d);
@@ -715,6 +791,7 @@ extern "C" lbm_status lbm_set_anisotropy(lbm_ctx* c, const float* shape, void* b
 {
     if (!c) return LBM_EINVAL;
     if (!c->ready) return fail(c, LBM_ESTATE, "context not initialised");
+    ++c->params_gen;  // the captured step graphs hold the old parameters
     if (!shape) {
         c->base.aniso = nullptr;
         return LBM_OK;
@@ -863,7 +940,12 @@ extern "C" int64_t lbm_fluid_count(const lbm_ctx* c) { return c ? c->n_store - c
 extern "C" const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
 extern "C" void lbm_destroy(lbm_ctx* c)
 {
-    if (c) l2_release(c);
+    if (c) {
+        l2_release(c);
+        for (cudaGraphExec_t& g : c->graph)
+            if (g) cudaGraphExecDestroy(g);
+        if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    }
     delete c;
 }
 
@@ -1242,6 +1324,7 @@ extern "C" lbm_status lbm_set_halo(lbm_ctx* c, int32_t lo_planes, int32_t hi_pla
     LBM_CUDA(cudaStreamSynchronize(c->stream), "halo set-up sync");
     c->base.n_general = (int)c->general.size();
     c->host_idx.clear();  // halo slots scatter nothing to host outputs
+    ++c->params_gen;
     c->halo_lo = lo_planes;
     c->halo_hi = hi_planes;
     return LBM_OK;
